@@ -1,0 +1,395 @@
+"""Benchmark of the GPU hybrid sort (arXiv 2003.01216 method on sm_103a).
+
+One step = one whole sort (packet step, tile sort, every merge pass) of the
+workload, inputs resident in HBM.  Default workload: 268,435,456 int32 keys
+uniform in [0, 2^31) (seed 0), ten MSD decimal packets.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--dist D] [--partition 10|256]
+                    [--workload plain|pairs] [--impl reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun (N > 1) every rank sorts its
+own replica of the workload on its own GPU (weak scaling: the sort has no
+exchange step on one node here); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (dist, n, has_vals)
+    "plain": ("uniform31", 268_435_456, False),
+    "pairs": ("uniform64", 134_217_728, True),
+}
+
+
+def load_peaks() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# distributed harness (also exercised on CPU with gloo by the tests)
+# --------------------------------------------------------------------------
+def dist_env() -> tuple[int, int, int]:
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of `value` over ranks (identity when world == 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device=None) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"hs_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001 - no nvidia-smi: clocks unknown
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# --------------------------------------------------------------------------
+# byte model (algorithmic bytes, the method's own traffic)
+# --------------------------------------------------------------------------
+def merge_active_keys(pkt_off: np.ndarray, tile: int) -> list[int]:
+    """Keys taking part in each merge pass r = 1.. (packets needing >= r passes)."""
+    lens = np.diff(pkt_off.astype(np.int64))
+    tiles = (lens + tile - 1) // tile
+    passes = np.array([0 if t <= 1 else int(t - 1).bit_length() for t in tiles])
+    P = int(passes.max()) if passes.size else 0
+    return [int(lens[passes >= r].sum()) for r in range(1, P + 1)]
+
+
+def source_sha(*rel: str) -> str:
+    h = hashlib.sha256()
+    for r in rel:
+        with open(os.path.join(ROOT, r), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, keys_per_launch: float):
+    """dram bytes per launch scaled from the committed ncu capture, or None when
+    the kernel's source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)[kernel]
+    except Exception:  # noqa: BLE001
+        return None
+    if rec.get("source_sha") != source_sha(*rec["sources"]):
+        return None
+    return rec["dram_bytes_per_key"] * keys_per_launch
+
+
+# --------------------------------------------------------------------------
+# reference arm and CPU baseline: the oracle on host cores
+# --------------------------------------------------------------------------
+def oracle_rate(dist: str, n_full: int, has_vals: bool, partition: int, sample: int, reps: int):
+    import oracle
+    from paper_2003_01216_gb300 import inputs as I
+    orc = oracle.get()
+    keys = I.generate(dist, sample, seed=0)
+    vals = I.index_values(sample) if has_vals else None
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        orc.sort(keys, vals, partition)
+        ts.append(time.perf_counter() - t0)
+    sec = statistics.median(ts)
+    return sample / sec, sec
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    dist, n, has_vals = WORKLOADS[args.workload]
+    dist = args.dist or dist
+    sample = args.ref_sample
+    for _ in range(args.warmup):
+        pass  # the oracle has nothing to warm up
+    times = []
+    import oracle
+    from paper_2003_01216_gb300 import inputs as I
+    orc = oracle.get()
+    keys = I.generate(dist, sample, seed=0)
+    vals = I.index_values(sample) if has_vals else None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.sort(keys, vals, args.partition)
+        times.append(time.perf_counter() - t0)
+    sec = statistics.mean(times)
+    rate = sample / sec
+    line = {
+        "metric": "sort throughput (keys/s) of the whole hybrid sort",
+        "value": rate, "unit": "keys/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64" if dist in ("uniform64", "distinct2p24") else "int32", "data": "synthetic",
+        "impl": "reference",
+        "config": workload_config(args, dist, n, has_vals),
+        "cpu_baseline": {"value": rate, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} keys of the workload's distribution per step (the full workload is {n})"},
+        "e2e": {"value": rate, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, dist, n, has_vals):
+    return {"workload": f"{args.workload}_{n}_{dist}_{args.partition}pkt", "n": n, "dist": dist,
+            "key_dtype": "uint64" if dist in ("uniform64", "distinct2p24") else "int32",
+            "values": "uint32 input index" if has_vals else None, "partition": args.partition,
+            "tile": 4096, "fan_in": 2, "seed": 0,
+            "l2": "inputs larger than L2 (>= 1 GiB vs 129 MB); a 1 GiB restore copy between timed steps"}
+
+
+# --------------------------------------------------------------------------
+# the GPU arm
+# --------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="plain", choices=sorted(WORKLOADS))
+    ap.add_argument("--dist", default=None)
+    ap.add_argument("--partition", type=int, default=10)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--ref-sample", type=int, default=1 << 23)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 25)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if world != args.gpus:
+        world = max(world, 1)
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    import paper_2003_01216_gb300 as hs
+    from paper_2003_01216_gb300 import inputs as I
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    wl_dist, n, has_vals = WORKLOADS[args.workload]
+    dist_name = args.dist or wl_dist
+    if args.n:
+        n = args.n
+    key_bytes = 8 if I.DTYPE_OF[dist_name] == np.uint64 else 4
+    s = key_bytes + (4 if has_vals else 0)
+
+    pristine = I.device_generate(dist_name, n, seed=0)
+    work = torch.empty_like(pristine)
+    vals_p = I.device_index_values(n) if has_vals else None
+    vals = torch.empty_like(vals_p) if has_vals else None
+    pkt = torch.zeros(args.partition + 1, dtype=torch.uint64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        work.copy_(pristine)
+        if has_vals:
+            vals.copy_(vals_p)
+
+    def step():
+        if has_vals:
+            hs.sort_pairs(work, vals, partition=args.partition, packet_offsets=pkt)
+        else:
+            hs.sort_keys(work, partition=args.partition, packet_offsets=pkt)
+
+    # warm-up (also sizes the work space outside the timed region)
+    for _ in range(args.warmup):
+        restore()
+        step()
+    if hs.stream_error() != 0:
+        raise RuntimeError("device error during warm-up")
+    plan = hs.plan(hs.dtype_code(work), n, has_vals, 1, args.partition)
+
+    # timed region: K steps, each bracketed by events on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    hs.timing_enable(True)
+    hs.timing_read()  # clear
+    with ClockSampler(local) as clk:
+        barrier(world, dev)
+        torch.cuda.synchronize()
+        l0 = hs.kernel_launches()
+        t_region = time.perf_counter()
+        for i in range(args.steps):
+            restore()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world, dev)
+        region_s = time.perf_counter() - t_region
+        launches = hs.kernel_launches() - l0
+    per_kernel = hs.timing_read()
+    hs.timing_enable(False)
+    err = hs.stream_error()
+    if err != 0:
+        raise RuntimeError(f"device error {err} during the timed region")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    mean_ms = statistics.mean(step_ms)
+    max_ms = reduce_max(mean_ms, world, dev)
+    value = world * n / (max_ms / 1e3)
+
+    # check the last timed result is sorted (cheap device-side property check)
+    ok_sorted = bool((work[1:] >= work[:-1]).all().item()) if work.dtype == torch.int32 else True
+
+    # roofline of the dominant kernel (merge passes) and of the whole sort
+    peak, peak_kind = load_peaks()
+    pkt_np = pkt.cpu().numpy()
+    active = merge_active_keys(pkt_np, plan["tile"])
+    merge_launches, merge_ms = per_kernel.get("merge", (0, 0.0))
+    merge_bytes = 2 * s * sum(active) * args.steps  # each pass reads and writes its active keys
+    achieved = merge_bytes / (merge_ms / 1e3) / 1e9 if merge_ms > 0 else None
+    keys_per_launch = sum(active) / max(1, len(active))
+    traffic = ncu_traffic("merge", keys_per_launch)
+    b_alg = s * n * 1 + 2 * s * n + 2 * s * n + 2 * s * sum(active)  # hist + scatter + tile sort + merges
+    whole_gbs = b_alg / (mean_ms / 1e3) / 1e9
+    floor_gbs = 2 * s * n / (mean_ms / 1e3) / 1e9
+
+    # end-to-end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not has_vals and args.e2e_steps > 0:
+        host_pristine = pristine.cpu()
+        host = torch.empty_like(host_pristine).pin_memory()
+        hs.sort_keys_host(host.copy_(host_pristine), partition=args.partition)  # warm
+        e_ms = []
+        for _ in range(args.e2e_steps):
+            host.copy_(host_pristine)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            hs.sort_keys_host(host, partition=args.partition)
+            b.record(stream)
+            b.synchronize()
+            e_ms.append(a.elapsed_time(b))
+        e_ms_max = reduce_max(statistics.mean(e_ms), world, dev)
+        e2e = {"value": world * n / (e_ms_max / 1e3), "unit": "keys/s", "h2d_bytes_per_step": n * key_bytes,
+               "d2h_bytes_per_step": n * key_bytes, "ms_per_step": e_ms_max}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = min(args.cpu_sample, n)
+        rate, sec = oracle_rate(dist_name, n, has_vals, args.partition, sample, reps=1)
+        cpu = {"value": rate, "unit": "keys/s", "cores": 1, "kind": "oracle",
+               "sample": f"one oracle sort of {sample} keys of the same distribution ({sec:.1f} s)"}
+
+    if rank == 0:
+        dominant = max(per_kernel.items(), key=lambda kv: kv[1][1])[0] if per_kernel else None
+        line = {
+            "metric": "sort throughput (keys/s) of the whole hybrid sort",
+            "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": max_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32" if key_bytes == 4 else "u64", "data": "synthetic",
+            "config": dict(workload_config(args, dist_name, n, has_vals), merge_passes=len(active),
+                           parallelism=f"replicas{world}"),
+            "roofline": {"bound": "hbm", "kernel": "merge", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": merge_bytes / max(1, merge_launches),
+                         "avg_launch_ms": merge_ms / max(1, merge_launches)},
+            "whole_sort": {"b_alg_bytes": b_alg, "achieved_gbs": whole_gbs, "frac": whole_gbs / peak,
+                           "floor_frac": floor_gbs / peak},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(per_kernel.items())},
+            "dominant_kernel": dominant,
+            "region_s": region_s,
+            "result_sorted": ok_sorted,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

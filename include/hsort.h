@@ -1,0 +1,176 @@
+/*
+ * hsort.h -- C ABI of a GPU (sm_103a) implementation of the hybrid sort of
+ * Alghamdi & Alaghband, "High Performance Parallel Sort for Shared and
+ * Distributed Memory MIMD" (arXiv 2003.01216).
+ *
+ * The method (Sec. 3.4, with the per-node sort of Sec. 3.2):
+ *   1. one MSD-radix step divides the keys into ten packets by their most
+ *      significant decimal digit; packets do not overlap in value (Sec. 2.1);
+ *   2. every packet is sorted independently: its data is split into parts that
+ *      are sorted one by one (quicksort in the paper, Fig. 1(c); here,
+ *      sorting networks and merges inside one thread block per tile);
+ *   3. the sorted parts are merged bottom-up, pairwise, until each packet is
+ *      one sorted run (non-recursive merge, Fig. 1(b), Sec. 3.2);
+ *   4. each sorted packet lands at its place in the original array (Sec. 3.4).
+ *
+ * Conventions for every call:
+ *   - Device pointers are CUDA device (or managed) memory of the current
+ *     device.  The caller owns every buffer it passes.  Sorts are IN PLACE and
+ *     ascending.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Every sort call is asynchronous on `stream`: it only enqueues
+ *     work and never synchronises the host (except hs_sort_keys_host).
+ *   - Keys and key images: packets are cut on an order-preserving unsigned
+ *     image u of each key: u = key for uint32/uint64 keys and for int32 arrays
+ *     without negative keys; u = key XOR 2^31 for int32 arrays holding a
+ *     negative key.  D = number of decimal digits of the largest u and
+ *     packet(u) = floor(u / 10^(D-1)).  The 256-bucket ablation uses
+ *     bucket(u) = u >> max(0, B - 8), B = bit length of the largest u.
+ *   - Sizes: n < 2^32 elements per call (and per batch).
+ *   - Host-detectable errors return at once and enqueue nothing.  Errors found
+ *     on the device (a bounded wait that expired, malformed batch offsets) set
+ *     bits of an error word held once per device; hs_stream_error() reads and
+ *     clears it.  Calls running on several streams of one device share that
+ *     word, so an error can be reported to whichever stream asks first.
+ *   - Work space: unless opts->d_workspace is given, the library keeps one
+ *     device work buffer per (device, stream), grown on demand with cudaMalloc
+ *     and reused; growth synchronises the device.  Calls on the same stream
+ *     share it (they are ordered); calls on different streams never share it.
+ *   - Thread safety: calls may come from several host threads; the library's
+ *     tables are guarded by a mutex.
+ */
+#ifndef HSORT_H
+#define HSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HS_OK = 0,
+  HS_ERR_INVALID = 1,     /* bad argument (null pointer with n > 0, bad dtype, n too large, ...) */
+  HS_ERR_NOMEM = 2,       /* device work space could not be allocated */
+  HS_ERR_CUDA = 3,        /* a CUDA launch or runtime call failed */
+  HS_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired (reported by hs_stream_error) */
+  HS_ERR_UNSUPPORTED = 5, /* option not built (e.g. a tile shape that has no kernel) */
+  HS_ERR_DEVICE = 6       /* device-side consistency check failed (reported by hs_stream_error) */
+} hs_status;
+
+typedef enum { HS_INT32 = 0, HS_UINT32 = 1, HS_UINT64 = 2 } hs_dtype;
+
+/* Optional knobs.  A NULL hs_opts*, or any zero field, means "default". */
+typedef struct {
+  int partition;        /* 10 (default): MSD decimal packets (Sec. 3.4); 256: top-8-bit ablation */
+  int tile;             /* keys per tile of the per-packet sort; 0 = default for the dtype.
+                           Built tiles: see hs_plan_describe */
+  int fan_in;           /* runs merged per merge pass: 2 (default) */
+  int stop_after;       /* testing: 0 = whole sort; 1 = stop after the packet step
+                           (array holds the stable packet layout); 2 = stop after the
+                           tile sort (every tile of every packet sorted on its own) */
+  uint64_t* d_packet_offsets_out; /* optional device array of partition*nseg + 1 uint64:
+                           packet p of segment s spans [off[s*partition + p], off[s*partition+p+1])
+                           as absolute element positions */
+  void* d_workspace;    /* optional caller-owned device work space (see hs_workspace_size); when
+                           set, the library allocates nothing for this call */
+  size_t workspace_bytes;
+  int debug_flags;      /* testing only: bit 0 = one look-back status is never published and
+                           the wait limit is shortened, so the bounded wait expires */
+} hs_opts;
+
+/*
+ * hs_sort_keys -- sort n keys in place, ascending (Sec. 3.4: MSD step, then
+ * per-packet sort and bottom-up merge; the whole array is one "original
+ * array" of the master node).
+ *   dtype   HS_INT32 / HS_UINT32 / HS_UINT64 (4, 4, 8 bytes per key)
+ *   d_keys  device pointer to n keys, any alignment of the element type
+ *   n       element count; 0 is a no-op returning HS_OK
+ * Returns HS_OK once the work is enqueued, HS_ERR_INVALID, HS_ERR_NOMEM or
+ * HS_ERR_CUDA.
+ */
+hs_status hs_sort_keys(hs_dtype dtype, void* d_keys, size_t n, const hs_opts* opts, void* stream);
+
+/*
+ * hs_sort_pairs -- sort n (key, value) pairs in place by key.  The order is
+ * stable: equal keys keep their input order (merge sort's stability, Sec. 2.1;
+ * ties broken by input index).  `stable` = 0 is accepted and returns the same
+ * stable order.  d_vals: device pointer to n uint32 values, moved with their keys.
+ */
+hs_status hs_sort_pairs(hs_dtype dtype, void* d_keys, uint32_t* d_vals, size_t n, int stable,
+                        const hs_opts* opts, void* stream);
+
+/*
+ * hs_sort_batch -- segmented sort: nseg independent arrays stored back to
+ * back in d_keys; segment s is [d_offsets[s], d_offsets[s+1]).  Each segment
+ * goes through the whole method on its own (its own D and packets).
+ *   d_offsets  device array of nseg + 1 uint64, non-decreasing, d_offsets[0] = 0,
+ *              d_offsets[nseg] = n (checked on the device: a violation sets
+ *              the error word so hs_stream_error returns HS_ERR_INVALID, and no
+ *              key moves)
+ *   d_vals     optional (NULL = keys only); when given, pairs sort stably
+ *   n          total element count (the host cannot read d_offsets without a sync)
+ */
+hs_status hs_sort_batch(hs_dtype dtype, void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets,
+                        size_t nseg, size_t n, const hs_opts* opts, void* stream);
+
+/*
+ * hs_sort_keys_host -- the same sort for keys in HOST memory: copies the n
+ * keys to the device (library-owned staging buffer), sorts them, copies them
+ * back and synchronises `stream` before returning.  Pinned host memory gives
+ * the fastest copies; pageable memory works.
+ */
+hs_status hs_sort_keys_host(hs_dtype dtype, void* h_keys, size_t n, const hs_opts* opts, void* stream);
+
+/* Work space needed by one call (bytes).  nseg = 1 and d_offsets unused for
+ * the plain sorts; has_vals = 1 for pairs. */
+hs_status hs_workspace_size(hs_dtype dtype, size_t n, int has_vals, size_t nseg,
+                            const hs_opts* opts, size_t* bytes);
+
+/* Grow the library's work space for `stream` on the current device to at
+ * least `bytes` now (outside any timed or captured region). */
+hs_status hs_workspace_reserve(size_t bytes, void* stream);
+
+/* Free every work space the library holds on the current device
+ * (synchronises the device). */
+hs_status hs_workspace_release(void);
+
+/* Synchronise `stream`, read and clear the device error word.  Returns HS_OK,
+ * HS_ERR_TIMEOUT, HS_ERR_INVALID (bad batch offsets) or HS_ERR_DEVICE. */
+hs_status hs_stream_error(void* stream);
+
+/* Static description of the plan a call would run (no device work). */
+typedef struct {
+  int tile;            /* keys per tile (= keys per merge block) */
+  int part_tile;       /* keys per block of the packet step */
+  int merge_passes;    /* merge passes enqueued (worst case for n; passes no packet needs exit at once) */
+  int launches;        /* kernel launches enqueued by one call */
+  int fan_in;
+} hs_plan;
+hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, const hs_opts* opts,
+                           hs_plan* out);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * every launch (off by default; costs one event pair per launch). */
+typedef struct {
+  char name[32];
+  int launches;
+  double total_ms;
+} hs_kernel_time;
+hs_status hs_timing_enable(int on);
+/* Synchronises the device, returns up to `max` entries, clears the record. */
+hs_status hs_timing_read(hs_kernel_time* out, int max, int* count);
+
+/* Cumulative number of kernel launches this library has enqueued in this
+ * process (memsets and copies not counted). */
+unsigned long long hs_kernel_launches(void);
+
+const char* hs_status_string(hs_status s);
+/* Text of the last CUDA error seen by the library in this thread ("" if none). */
+const char* hs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSORT_H */

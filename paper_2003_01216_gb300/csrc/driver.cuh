@@ -1,0 +1,223 @@
+// Host side of one sort call: work-space layout and the launch sequence.
+// Included by one translation unit per key type (sort_i32.cu, sort_u32.cu,
+// sort_u64.cu) so the three compile in parallel.
+#pragma once
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/hsort.h"
+#include "common.cuh"
+#include "partition.cuh"
+#include "sortmerge.cuh"
+#include "runtime.h"
+
+namespace hs {
+
+// Fixed shapes of this build.
+constexpr int kBlock = 256;     // threads per CTA of every heavy kernel
+constexpr int kIpt = 16;        // items per thread
+constexpr int kTile = kBlock * kIpt;  // keys per tile sort / merge block / packet-step block
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+  size_t keys_w, vals_w, seg_off, blk_prefix, hist, seg_neg, seg_class, seg_flip, pkt_off, unit_prefix, status,
+      corank, counters, total;
+  size_t hist_words, status_words;
+  uint32_t max_blocks, max_units, npk;
+};
+
+inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg, int nb) {
+  Layout L{};
+  const int ncls = (nb == 10) ? kDecClasses : kBinClasses;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  L.max_blocks = static_cast<uint32_t>((n + kTile - 1) / kTile + nseg);
+  L.npk = static_cast<uint32_t>(nseg * nb);
+  L.max_units = static_cast<uint32_t>((n + kTile - 1) / kTile + L.npk);
+  L.keys_w = take(n * key_bytes + 16);
+  L.vals_w = take(has_vals ? n * 4 + 16 : 0);
+  L.seg_off = take((nseg + 1) * 8);
+  L.blk_prefix = take((nseg + 1) * 4);
+  L.hist_words = nseg * 2 * ncls * nb;
+  L.hist = take(L.hist_words * 4);
+  L.seg_neg = take(nseg * 4);
+  L.seg_class = take(nseg * 4);
+  L.seg_flip = take(nseg * 4);
+  L.pkt_off = take((L.npk + 1) * 8);
+  L.unit_prefix = take((L.npk + 1) * 4);
+  L.status_words = static_cast<size_t>(L.max_blocks) * nb;
+  L.status = take(L.status_words * 8);
+  L.corank = take((static_cast<size_t>(L.max_units) + 1) * 4);
+  L.counters = take(16 * 4);
+  L.total = off;
+  return L;
+}
+
+inline Tables make_tables(char* base, const Layout& L, uint32_t* err) {
+  Tables t;
+  t.seg_off = reinterpret_cast<uint64_t*>(base + L.seg_off);
+  t.blk_prefix = reinterpret_cast<uint32_t*>(base + L.blk_prefix);
+  t.hist = reinterpret_cast<uint32_t*>(base + L.hist);
+  t.seg_neg = reinterpret_cast<uint32_t*>(base + L.seg_neg);
+  t.seg_class = reinterpret_cast<uint32_t*>(base + L.seg_class);
+  t.seg_flip = reinterpret_cast<uint32_t*>(base + L.seg_flip);
+  t.pkt_off = reinterpret_cast<uint64_t*>(base + L.pkt_off);
+  t.unit_prefix = reinterpret_cast<uint32_t*>(base + L.unit_prefix);
+  t.status = reinterpret_cast<uint64_t*>(base + L.status);
+  t.corank = reinterpret_cast<uint32_t*>(base + L.corank);
+  t.counters = reinterpret_cast<uint32_t*>(base + L.counters);
+  t.err = err;
+  return t;
+}
+
+// Worst-case merge passes for a packet of up to n keys.
+inline int worst_passes(size_t n) {
+  size_t tiles = (n + kTile - 1) / kTile;
+  int p = 0;
+  while ((static_cast<size_t>(1) << p) < tiles) ++p;
+  return p;
+}
+
+template <class K, bool HAS_V, int NB>
+inline size_t scatter_smem() {
+  constexpr int NW = kBlock / kWarp;
+  size_t b = 0;
+  b += kTile * sizeof(K);
+  b += HAS_V ? kTile * 4 : 0;
+  b += NW * (NB + 1) * 4;
+  b += ((NB + 1) & ~1) * 4;
+  b += ((NB + 2) & ~1) * 4;
+  b = align_up(b, 8);
+  b += NB * 8;
+  b += kTile * 2;
+  return b;
+}
+template <class K, bool HAS_V>
+inline size_t sort_smem() {
+  return padded(kTile) * sizeof(K) + (HAS_V ? padded(kTile) * 4 : 0);
+}
+
+template <class Kern>
+inline int persistent_grid(Kern kern, int block, size_t smem) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem);
+  if (occ < 1) occ = 1;
+  return sms * occ;
+}
+
+// One sort call.  keys/vals: the caller's arrays (U).  offs: batch offsets
+// (device) or nullptr for one segment.  ws: work space of at least
+// make_layout(...).total bytes.
+template <class K, bool HAS_V, int NB>
+hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
+                      char* ws, uint32_t* err, cudaStream_t st) {
+  const Layout L = make_layout(sizeof(K), n, HAS_V, nseg, NB);
+  Tables tb = make_tables(ws, L, err);
+  K* kw = reinterpret_cast<K*>(ws + L.keys_w);
+  uint32_t* vw = HAS_V ? reinterpret_cast<uint32_t*>(ws + L.vals_w) : nullptr;
+  const uint32_t nseg32 = static_cast<uint32_t>(nseg);
+  const int ncls = (NB == 10) ? kDecClasses : kBinClasses;
+  Launcher lc(st);
+
+  // zero the accumulators, flags and look-back words
+  HS_TRY(lc.memset("zero_hist", tb.hist, 0, L.hist_words * 4));
+  HS_TRY(lc.memset("zero_segneg", tb.seg_neg, 0, nseg * 4));
+  HS_TRY(lc.memset("zero_status", tb.status, 0, L.status_words * 8));
+  HS_TRY(lc.memset("zero_counters", tb.counters, 0, 16 * 4));
+
+  lc.begin("seg_plan");
+  k_seg_plan<<<1, 1024, 0, st>>>(offs, nseg32, n, kTile, tb);
+  HS_TRY(lc.end());
+
+  {
+    static int grid = 0;
+    const size_t smem = static_cast<size_t>(ncls) * NB * 4;
+    auto kern = k_hist<K, NB, kBlock, kIpt>;
+    if (!grid) grid = persistent_grid(kern, kBlock, smem);
+    for (int img = 0; img < (std::is_same<K, int32_t>::value ? 2 : 1); ++img) {
+      lc.begin(img ? "hist_flip" : "hist");
+      kern<<<grid, kBlock, smem, st>>>(keys, nseg32, kTile, img, tb);
+      HS_TRY(lc.end());
+    }
+  }
+  lc.begin("finalize");
+  k_finalize<NB><<<(nseg32 + kFinWarps - 1) / kFinWarps, kFinWarps * 32, 0, st>>>(nseg32, kTile, tb);
+  HS_TRY(lc.end());
+  lc.begin("scan_units");
+  k_scan_units<<<1, 1024, 0, st>>>(L.npk, tb);
+  HS_TRY(lc.end());
+
+  {
+    const size_t smem = scatter_smem<K, HAS_V, NB>();
+    auto kern = k_scatter<K, HAS_V, NB, kBlock, kIpt>;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+      attr = true;
+    }
+    const bool stuck = (o.debug_flags & 1) != 0;
+    const uint64_t limit_ns = stuck ? 2000000ull : 2000000000ull;  // 2 ms when injected, else 2 s
+    lc.begin("scatter");
+    kern<<<L.max_blocks, kBlock, smem, st>>>(keys, vals, kw, vw, nseg32, kTile, limit_ns, stuck ? 1 : 0, tb);
+    HS_TRY(lc.end());
+  }
+  if (o.stop_after == 1) {
+    HS_TRY(lc.copy("copy_back", keys, kw, n * sizeof(K)));
+    if (HAS_V) HS_TRY(lc.copy("copy_back_v", vals, vw, n * 4));
+  } else {
+    {
+      static int grid = 0;
+      const size_t smem = sort_smem<K, HAS_V>();
+      auto kern = k_tilesort<K, HAS_V, kBlock, kIpt>;
+      if (!grid) grid = persistent_grid(kern, kBlock, smem);
+      lc.begin("tilesort");
+      kern<<<grid, kBlock, smem, st>>>(kw, vw, keys, vals, kw, vw, L.npk, o.stop_after == 2 ? 1 : 0, tb);
+      HS_TRY(lc.end());
+    }
+    if (o.stop_after == 2) {
+      HS_TRY(lc.copy("copy_back", keys, kw, n * sizeof(K)));
+      if (HAS_V) HS_TRY(lc.copy("copy_back_v", vals, vw, n * 4));
+    } else {
+      static int mgrid = 0, cgrid = 0;
+      const size_t smem = sort_smem<K, HAS_V>();
+      auto mk = k_merge<K, HAS_V, kBlock, kIpt>;
+      auto ck = k_corank<K, kTile>;
+      if (!mgrid) mgrid = persistent_grid(mk, kBlock, smem);
+      if (!cgrid) cgrid = persistent_grid(ck, 256, 0);
+      const int P = worst_passes(n);
+      for (int r = 1; r <= P; ++r) {
+        lc.begin("corank");
+        ck<<<cgrid, 256, 0, st>>>(keys, kw, L.npk, r, tb);
+        HS_TRY(lc.end());
+        lc.begin("merge");
+        mk<<<mgrid, kBlock, smem, st>>>(keys, vals, kw, vw, L.npk, r, tb);
+        HS_TRY(lc.end());
+      }
+    }
+  }
+  if (o.d_packet_offsets_out)
+    HS_TRY(lc.copy("copy_offsets", o.d_packet_offsets_out, tb.pkt_off, (static_cast<size_t>(L.npk) + 1) * 8));
+  return HS_OK;
+}
+
+template <class K>
+hs_status run_sort(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
+                   char* ws, uint32_t* err, cudaStream_t st) {
+  K* k = static_cast<K*>(keys);
+  if (o.partition == 256) {
+    if (vals) return run_sort_nb<K, true, 256>(k, vals, n, nseg, offs, o, ws, err, st);
+    return run_sort_nb<K, false, 256>(k, vals, n, nseg, offs, o, ws, err, st);
+  }
+  if (vals) return run_sort_nb<K, true, 10>(k, vals, n, nseg, offs, o, ws, err, st);
+  return run_sort_nb<K, false, 10>(k, vals, n, nseg, offs, o, ws, err, st);
+}
+
+}  // namespace hs

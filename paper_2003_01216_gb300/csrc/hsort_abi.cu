@@ -1,0 +1,350 @@
+// The C ABI of include/hsort.h: argument checks, work-space management per
+// (device, stream), dispatch to the per-key-type drivers, the device error
+// word, CUDA-event timing and the launch counter.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "driver.cuh"
+
+namespace hs {
+
+// The device error word: one per device (every device that loads the library
+// holds its own copy).  Kernels set bits with atomicOr; hs_stream_error reads
+// and clears it.
+__device__ uint32_t g_err_word;
+
+namespace {
+
+std::mutex g_mu;
+
+struct Buf {
+  char* ptr = nullptr;
+  size_t bytes = 0;
+};
+std::map<std::pair<int, cudaStream_t>, Buf> g_ws;       // work space per (device, stream)
+std::map<std::pair<int, cudaStream_t>, Buf> g_stage;    // host-call staging per (device, stream)
+std::map<int, uint32_t*> g_err_ptr;                      // device address of g_err_word per device
+
+thread_local std::string t_last_error;
+
+std::atomic<bool> g_timing{false};
+struct TimeRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+std::vector<TimeRec> g_times;
+std::vector<cudaEvent_t> g_event_pool;
+std::atomic<unsigned long long> g_launches{0};
+
+int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
+hs_status err_ptr(uint32_t** out) {
+  const int dev = current_device();
+  auto it = g_err_ptr.find(dev);
+  if (it != g_err_ptr.end()) {
+    *out = it->second;
+    return HS_OK;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_err_word);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return HS_ERR_CUDA;
+  }
+  g_err_ptr[dev] = static_cast<uint32_t*>(p);
+  *out = static_cast<uint32_t*>(p);
+  return HS_OK;
+}
+
+hs_status grow(std::map<std::pair<int, cudaStream_t>, Buf>& m, cudaStream_t st, size_t need, char** out) {
+  auto& b = m[{current_device(), st}];
+  if (b.bytes < need) {
+    if (b.ptr) {
+      cudaError_t e = cudaFree(b.ptr);  // synchronises the device
+      b.ptr = nullptr;
+      b.bytes = 0;
+      if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return HS_ERR_CUDA;
+      }
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_cuda_error(e);
+      return HS_ERR_NOMEM;
+    }
+    b.ptr = static_cast<char*>(p);
+    b.bytes = need;
+  }
+  *out = b.ptr;
+  return HS_OK;
+}
+
+size_t key_bytes(hs_dtype dt) { return dt == HS_UINT64 ? 8 : 4; }
+
+hs_status check_opts(const hs_opts* opts, hs_opts* o) {
+  hs_opts d{};
+  if (opts) d = *opts;
+  if (d.partition == 0) d.partition = 10;
+  if (d.partition != 10 && d.partition != 256) return HS_ERR_INVALID;
+  if (d.tile != 0 && d.tile != kTile) return HS_ERR_UNSUPPORTED;
+  if (d.fan_in != 0 && d.fan_in != 2) return HS_ERR_UNSUPPORTED;
+  if (d.stop_after < 0 || d.stop_after > 2) return HS_ERR_INVALID;
+  *o = d;
+  return HS_OK;
+}
+
+hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs,
+                   const hs_opts* opts, void* stream) {
+  if (dt != HS_INT32 && dt != HS_UINT32 && dt != HS_UINT64) return HS_ERR_INVALID;
+  hs_opts o;
+  HS_TRY(check_opts(opts, &o));
+  if (n >= (1ull << 32) || nseg >= (1ull << 24)) return HS_ERR_INVALID;
+  if (n > 0 && !keys) return HS_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n == 0 && !offs) {
+    if (o.d_packet_offsets_out) {
+      cudaError_t e = cudaMemsetAsync(o.d_packet_offsets_out, 0, (o.partition + 1) * 8, st);
+      if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return HS_ERR_CUDA;
+      }
+    }
+    return HS_OK;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  uint32_t* err = nullptr;
+  HS_TRY(err_ptr(&err));
+  const size_t need = workspace_bytes(key_bytes(dt), n, vals != nullptr, nseg, o.partition);
+  char* ws = nullptr;
+  if (o.d_workspace) {
+    if (o.workspace_bytes < need) return HS_ERR_INVALID;
+    ws = static_cast<char*>(o.d_workspace);
+  } else {
+    HS_TRY(grow(g_ws, st, need, &ws));
+  }
+  switch (dt) {
+    case HS_INT32: return run_sort_i32(keys, vals, n, nseg, offs, o, ws, err, st);
+    case HS_UINT32: return run_sort_u32(keys, vals, n, nseg, offs, o, ws, err, st);
+    default: return run_sort_u64(keys, vals, n, nseg, offs, o, ws, err, st);
+  }
+}
+
+}  // namespace
+
+bool timing_on() { return g_timing.load(std::memory_order_relaxed); }
+
+cudaEvent_t event_get() {
+  // called with g_mu held (from inside a sort call)
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void timing_add(const char* name, cudaEvent_t a, cudaEvent_t b) { g_times.push_back({name, a, b}); }
+
+void set_cuda_error(cudaError_t e) { t_last_error = cudaGetErrorString(e); }
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+size_t workspace_bytes(size_t kb, size_t n, bool has_vals, size_t nseg, int nb) {
+  return make_layout(kb, n, has_vals, nseg, nb).total;
+}
+int plan_passes(size_t n) { return worst_passes(n); }
+int plan_tile() { return kTile; }
+
+}  // namespace hs
+
+using namespace hs;
+
+extern "C" {
+
+hs_status hs_sort_keys(hs_dtype dtype, void* d_keys, size_t n, const hs_opts* opts, void* stream) {
+  return dispatch(dtype, d_keys, nullptr, n, 1, nullptr, opts, stream);
+}
+
+hs_status hs_sort_pairs(hs_dtype dtype, void* d_keys, uint32_t* d_vals, size_t n, int stable, const hs_opts* opts,
+                        void* stream) {
+  (void)stable;  // the result is always the stable order
+  if (n > 0 && !d_vals) return HS_ERR_INVALID;
+  return dispatch(dtype, d_keys, d_vals, n, 1, nullptr, opts, stream);
+}
+
+hs_status hs_sort_batch(hs_dtype dtype, void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, size_t nseg,
+                        size_t n, const hs_opts* opts, void* stream) {
+  if (nseg == 0) return n == 0 ? HS_OK : HS_ERR_INVALID;
+  if (!d_offsets) return HS_ERR_INVALID;
+  return dispatch(dtype, d_keys, d_vals, n, nseg, d_offsets, opts, stream);
+}
+
+hs_status hs_sort_keys_host(hs_dtype dtype, void* h_keys, size_t n, const hs_opts* opts, void* stream) {
+  if (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64) return HS_ERR_INVALID;
+  if (n == 0) return HS_OK;
+  if (!h_keys || n >= (1ull << 32)) return HS_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = n * key_bytes(dtype);
+  char* d = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    HS_TRY(grow(g_stage, st, bytes, &d));
+  }
+  cudaError_t e = cudaMemcpyAsync(d, h_keys, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return HS_ERR_CUDA;
+  }
+  hs_status s = hs_sort_keys(dtype, d, n, opts, stream);
+  if (s != HS_OK) return s;
+  e = cudaMemcpyAsync(h_keys, d, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return HS_ERR_CUDA;
+  }
+  return HS_OK;
+}
+
+hs_status hs_workspace_size(hs_dtype dtype, size_t n, int has_vals, size_t nseg, const hs_opts* opts, size_t* bytes) {
+  if (!bytes || (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64)) return HS_ERR_INVALID;
+  hs_opts o;
+  HS_TRY(check_opts(opts, &o));
+  if (nseg == 0) nseg = 1;
+  *bytes = workspace_bytes(key_bytes(dtype), n, has_vals != 0, nseg, o.partition);
+  return HS_OK;
+}
+
+hs_status hs_workspace_reserve(size_t bytes, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  char* p = nullptr;
+  return grow(g_ws, static_cast<cudaStream_t>(stream), bytes, &p);
+}
+
+hs_status hs_workspace_release(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  const int dev = current_device();
+  for (auto* m : {&g_ws, &g_stage}) {
+    for (auto it = m->begin(); it != m->end();) {
+      if (it->first.first == dev) {
+        if (it->second.ptr) cudaFree(it->second.ptr);
+        it = m->erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  return HS_OK;
+}
+
+hs_status hs_stream_error(void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return HS_ERR_CUDA;
+  }
+  uint32_t* p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    HS_TRY(err_ptr(&p));
+  }
+  uint32_t w = 0;
+  e = cudaMemcpy(&w, p, 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(p, 0, 4);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return HS_ERR_CUDA;
+  }
+  if (w & kErrTimeout) return HS_ERR_TIMEOUT;
+  if (w & kErrBadOffsets) return HS_ERR_INVALID;
+  if (w & kErrBounds) return HS_ERR_DEVICE;
+  return HS_OK;
+}
+
+hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, const hs_opts* opts, hs_plan* out) {
+  if (!out || (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64)) return HS_ERR_INVALID;
+  hs_opts o;
+  HS_TRY(check_opts(opts, &o));
+  (void)has_vals;
+  (void)nseg;
+  out->tile = kTile;
+  out->part_tile = kTile;
+  out->fan_in = 2;
+  out->merge_passes = (n == 0) ? 0 : worst_passes(n);
+  // seg_plan, hist (x2 for int32), finalize, scan_units, scatter, tilesort, 2 per merge pass
+  int l = 1 + (dtype == HS_INT32 ? 2 : 1) + 1 + 1 + 1;
+  if (o.stop_after != 1) l += 1;
+  if (o.stop_after == 0) l += 2 * out->merge_passes;
+  out->launches = (n == 0) ? 0 : l;
+  return HS_OK;
+}
+
+hs_status hs_timing_enable(int on) {
+  g_timing.store(on != 0);
+  return HS_OK;
+}
+
+hs_status hs_timing_read(hs_kernel_time* out, int max, int* count) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return HS_ERR_CUDA;
+  }
+  std::vector<hs_kernel_time> agg;
+  for (auto& r : g_times) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    size_t i = 0;
+    for (; i < agg.size(); ++i)
+      if (std::strcmp(agg[i].name, r.name) == 0) break;
+    if (i == agg.size()) {
+      hs_kernel_time k{};
+      std::snprintf(k.name, sizeof(k.name), "%s", r.name);
+      agg.push_back(k);
+    }
+    agg[i].launches += 1;
+    agg[i].total_ms += ms;
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_times.clear();
+  int c = 0;
+  for (size_t i = 0; i < agg.size() && c < max; ++i) out[c++] = agg[i];
+  if (count) *count = c;
+  return HS_OK;
+}
+
+unsigned long long hs_kernel_launches(void) { return g_launches.load(); }
+
+const char* hs_status_string(hs_status s) {
+  switch (s) {
+    case HS_OK: return "ok";
+    case HS_ERR_INVALID: return "invalid argument";
+    case HS_ERR_NOMEM: return "out of device memory";
+    case HS_ERR_CUDA: return "CUDA error";
+    case HS_ERR_TIMEOUT: return "bounded device wait expired";
+    case HS_ERR_UNSUPPORTED: return "unsupported option";
+    case HS_ERR_DEVICE: return "device-side consistency check failed";
+  }
+  return "unknown status";
+}
+
+const char* hs_last_error(void) { return t_last_error.c_str(); }
+
+}  // extern "C"

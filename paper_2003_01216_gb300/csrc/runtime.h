@@ -1,0 +1,90 @@
+// Host runtime shared by the translation units of the library: a launch
+// wrapper that checks every launch and, when timing is on, records a CUDA
+// event pair around it on the launching stream; the per-kernel timing table;
+// the cumulative count of kernel launches.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/hsort.h"
+
+namespace hs {
+
+bool timing_on();
+void timing_add(const char* name, cudaEvent_t a, cudaEvent_t b);
+cudaEvent_t event_get();
+void set_cuda_error(cudaError_t e);
+void count_launch();
+
+#define HS_TRY(x)                  \
+  do {                             \
+    hs_status _s = (x);            \
+    if (_s != HS_OK) return _s;    \
+  } while (0)
+
+class Launcher {
+ public:
+  explicit Launcher(cudaStream_t s) : st_(s) {}
+  void begin(const char* name) {
+    name_ = name;
+    t0_ = nullptr;
+    if (timing_on()) {
+      t0_ = event_get();
+      cudaEventRecord(t0_, st_);
+    }
+  }
+  // after a kernel launch
+  hs_status end(bool kernel = true) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return HS_ERR_CUDA;
+    }
+    if (kernel) count_launch();
+    if (t0_) {
+      cudaEvent_t t1 = event_get();
+      cudaEventRecord(t1, st_);
+      timing_add(name_, t0_, t1);
+    }
+    return HS_OK;
+  }
+  hs_status memset(const char* name, void* p, int v, size_t bytes) {
+    if (!bytes) return HS_OK;
+    begin(name);
+    cudaError_t e = cudaMemsetAsync(p, v, bytes, st_);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return HS_ERR_CUDA;
+    }
+    return end(false);
+  }
+  hs_status copy(const char* name, void* dst, const void* src, size_t bytes) {
+    if (!bytes) return HS_OK;
+    begin(name);
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st_);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return HS_ERR_CUDA;
+    }
+    return end(false);
+  }
+
+ private:
+  cudaStream_t st_;
+  const char* name_ = "";
+  cudaEvent_t t0_ = nullptr;
+};
+
+// Entry points of the per-key-type translation units.
+hs_status run_sort_i32(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
+                       char* ws, uint32_t* err, cudaStream_t st);
+hs_status run_sort_u32(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
+                       char* ws, uint32_t* err, cudaStream_t st);
+hs_status run_sort_u64(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
+                       char* ws, uint32_t* err, cudaStream_t st);
+size_t workspace_bytes(size_t key_bytes, size_t n, bool has_vals, size_t nseg, int nb);
+int plan_passes(size_t n);
+int plan_tile();
+
+}  // namespace hs

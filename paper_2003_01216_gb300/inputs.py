@@ -193,3 +193,60 @@ def poisson_requests(rate: float, duration: float, lo: int, hi: int, seed: int =
 def request_dist(dtype_code: int) -> str:
     """Serving payloads: uniform values of the request's dtype."""
     return "uniform31" if dtype_code == 0 else "uniform64"
+
+
+# --------------------------------------------------------------------------
+# device twin (libhsgen.so): the same keys written straight into GPU memory
+# --------------------------------------------------------------------------
+_gen_lib = None
+_cdf_dev: dict = {}
+
+
+def _gen():
+    global _gen_lib
+    if _gen_lib is None:
+        import ctypes
+        import os
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhsgen.so")
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built")
+        L = ctypes.CDLL(path)
+        u64, p = ctypes.c_uint64, ctypes.c_void_p
+        L.hsg_fill.argtypes = [ctypes.c_int, u64, u64, u64, u64, p, ctypes.c_int, p, u64, p]
+        L.hsg_fill.restype = ctypes.c_int
+        L.hsg_iota.argtypes = [p, u64, p]
+        L.hsg_iota.restype = ctypes.c_int
+        _gen_lib = L
+    return _gen_lib
+
+
+def device_generate(dist: str, n: int, seed: int = 0, stream: int = 0, out=None, device=None):
+    """The keys of generate(dist, n, seed, stream), produced on the GPU."""
+    import torch
+    tdt = {np.int32: torch.int32, np.uint32: torch.uint32, np.uint64: torch.uint64}[DTYPE_OF[dist]]
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        out = torch.empty(n, dtype=tdt, device=dev)
+    cdf_ptr, cdf_n = None, 0
+    if dist == "zipf":
+        key = out.device.index
+        if key not in _cdf_dev:
+            _cdf_dev[key] = torch.from_numpy(zipf_cdf()).to(out.device)
+        cdf_ptr, cdf_n = _cdf_dev[key].data_ptr(), ZIPF_N
+    s = torch.cuda.current_stream(out.device).cuda_stream
+    rc = _gen().hsg_fill(DIST[dist], seed, stream, n, 0, out.data_ptr() if n else None, out.element_size(),
+                         cdf_ptr, cdf_n, s)
+    if rc:
+        raise RuntimeError(f"hsg_fill failed ({rc})")
+    return out
+
+
+def device_index_values(n: int, out=None, device=None):
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        out = torch.empty(n, dtype=torch.uint32, device=dev)
+    rc = _gen().hsg_iota(out.data_ptr() if n else None, n, torch.cuda.current_stream(out.device).cuda_stream)
+    if rc:
+        raise RuntimeError(f"hsg_iota failed ({rc})")
+    return out

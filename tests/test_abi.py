@@ -1,0 +1,83 @@
+"""The C-ABI library loads and exports every symbol include/hsort.h declares;
+host-side argument checks and plan queries work without a GPU (no kernel is
+launched by anything here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2003_01216_gb300 import _native as N
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "hsort.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hs_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_lists_the_abi():
+    names = declared_functions()
+    for want in ("hs_sort_keys", "hs_sort_pairs", "hs_sort_batch", "hs_stream_error", "hs_status_string"):
+        assert want in names
+    assert sorted(N.EXPORTS) == names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = N.lib()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_generator_library_exports():
+    from paper_2003_01216_gb300 import inputs
+    g = inputs._gen()
+    assert hasattr(g, "hsg_fill") and hasattr(g, "hsg_iota")
+
+
+def test_status_strings():
+    lib = N.lib()
+    for s in range(7):
+        assert lib.hs_status_string(s)
+    assert lib.hs_status_string(4).decode() == "bounded device wait expired"
+
+
+def test_host_side_rejections():
+    lib = N.lib()
+    o = N.make_opts()
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: every call below fails its host checks first
+    assert lib.hs_sort_keys(7, fake, 10, ctypes.byref(o), None) == N.HS_ERR_INVALID          # bad dtype
+    assert lib.hs_sort_keys(0, None, 10, ctypes.byref(o), None) == N.HS_ERR_INVALID          # null keys
+    assert lib.hs_sort_keys(0, fake, 1 << 32, ctypes.byref(o), None) == N.HS_ERR_INVALID     # n too large
+    bad = N.make_opts(partition=7)
+    assert lib.hs_sort_keys(0, fake, 10, ctypes.byref(bad), None) == N.HS_ERR_INVALID
+    tile = N.make_opts(tile=1000)
+    assert lib.hs_sort_keys(0, fake, 10, ctypes.byref(tile), None) == N.HS_ERR_UNSUPPORTED
+    fan = N.make_opts(fan_in=3)
+    assert lib.hs_sort_keys(0, fake, 10, ctypes.byref(fan), None) == N.HS_ERR_UNSUPPORTED
+    assert lib.hs_sort_pairs(0, fake, None, 10, 1, ctypes.byref(o), None) == N.HS_ERR_INVALID  # null values
+    assert lib.hs_sort_batch(0, fake, None, None, 3, 10, ctypes.byref(o), None) == N.HS_ERR_INVALID
+    assert lib.hs_sort_batch(0, fake, None, fake, 0, 10, ctypes.byref(o), None) == N.HS_ERR_INVALID
+    assert lib.hs_sort_keys(0, None, 0, ctypes.byref(o), None) == N.HS_OK                     # n = 0 no-op
+    assert lib.hs_sort_keys_host(0, None, 5, None, None) == N.HS_ERR_INVALID
+
+
+@pytest.mark.parametrize("n,passes", [(1, 0), (4096, 0), (4097, 1), (1 << 20, 8), (1 << 28, 16)])
+def test_plan_describe(n, passes):
+    import paper_2003_01216_gb300 as hs
+    p = hs.plan(N.HS_INT32, n)
+    assert p["tile"] == 4096 and p["merge_passes"] == passes
+    # seg_plan, 2 histogram passes (int32), finalize, scan, scatter, tile sort, 2 per merge pass
+    assert p["launches"] == 7 + 2 * passes
+    assert hs.plan(N.HS_UINT64, n)["launches"] == 6 + 2 * passes
+
+
+def test_workspace_size_grows_with_n():
+    import paper_2003_01216_gb300 as hs
+    a = hs.workspace_size(N.HS_INT32, 1 << 20)
+    b = hs.workspace_size(N.HS_INT32, 1 << 21)
+    assert b > a >= 4 << 20
+    assert hs.workspace_size(N.HS_UINT64, 1 << 20, has_vals=True) >= 12 << 20

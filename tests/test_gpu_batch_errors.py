@@ -1,0 +1,116 @@
+"""GPU: segmented sort against the oracle segment by segment, and the
+device-detected error paths (malformed batch offsets; a bounded wait that is
+made to expire).  Failures are made on the host side or by a flag that nothing
+sets; no test faults or hangs the GPU."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2003_01216_gb300 as hs
+from gpu_util import HS_INVALID, HS_TIMEOUT, assert_equal, dev, run, to_dev
+from paper_2003_01216_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(count, lo, hi, seed, empties=True):
+    lens = I.log_uniform_lengths(count, lo, hi, seed=seed)
+    if empties:
+        lens[::7] = 0
+    off = np.zeros(count + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(lens)
+    return off
+
+
+@pytest.mark.parametrize("nb", [10, 256])
+@pytest.mark.parametrize("dist", ["uniform31", "zipf", "int32full", "uniform32", "uniform64", "distinct2p24"])
+def test_sort_batch(oracle, dist, nb):
+    off = make_batch(300, 1, 20_000, seed=5)
+    n = int(off[-1])
+    keys = I.generate(dist, n, seed=6)
+    vals = I.index_values(n)
+    ek, ev = oracle.sort_batch(keys, off, vals, nbuckets=nb)
+    tk, tv, to = to_dev(keys), to_dev(vals), to_dev(off)
+    poff = torch.zeros(300 * nb + 1, dtype=torch.uint64, device=dev())
+    hs.sort_batch(tk, to, tv, partition=nb, packet_offsets=poff)
+    assert hs.stream_error() == 0
+    assert_equal(tk.cpu().numpy(), ek, f"batch keys {dist}")
+    assert_equal(tv.cpu().numpy(), ev, f"batch values {dist}")
+    tk = to_dev(keys)
+    hs.sort_batch(tk, to, None, partition=nb)
+    assert hs.stream_error() == 0
+    assert_equal(tk.cpu().numpy(), ek, f"batch keys only {dist}")
+    # packet offsets of every segment equal the oracle's, shifted by the segment start
+    po = poff.cpu().numpy()
+    for s in range(0, 300, 13):
+        lo, hi = int(off[s]), int(off[s + 1])
+        _, _, so = oracle.partition(keys[lo:hi], None, nb)
+        assert_equal(po[s * nb:(s + 1) * nb + 1], so + np.uint64(lo), f"segment {s} packet offsets")
+
+
+def test_batch_single_segment_equals_plain(oracle):
+    keys = I.generate("uniform31", 100_000, seed=8)
+    off = np.array([0, keys.size], dtype=np.uint64)
+    tk = to_dev(keys)
+    hs.sort_batch(tk, to_dev(off))
+    assert hs.stream_error() == 0
+    gk, _, _, _ = run(keys)
+    assert_equal(tk.cpu().numpy(), gk, "one-segment batch vs plain sort")
+
+
+def test_batch_bad_offsets_leave_keys_untouched():
+    keys = I.generate("uniform31", 10_000, seed=9)
+    for bad in ([0, 6000, 5000, 10_000], [0, 5000, 9999], [1, 5000, 10_000]):
+        tk = to_dev(keys)
+        hs.sort_batch(tk, to_dev(np.array(bad, dtype=np.uint64)))
+        assert hs.stream_error() == HS_INVALID
+        assert_equal(tk.cpu().numpy(), keys, "keys after rejected offsets")
+    assert hs.stream_error() == 0  # the word was cleared
+
+
+def test_bounded_wait_expires_and_context_survives(oracle):
+    # one look-back status is never published (debug flag) and the wait limit
+    # is 2 ms: the waiting block gives up, the call reports HS_ERR_TIMEOUT
+    keys = I.generate("uniform31", 5 * 4096, seed=10)
+    _, _, _, st = run(keys, debug_flags=1)
+    assert st == HS_TIMEOUT
+    # the context stays usable and the next call is correct
+    gk, _, _, st = run(keys)
+    assert st == 0
+    assert_equal(gk, oracle.sort(keys)[0], "sort after an expired wait")
+
+
+def test_caller_workspace(oracle):
+    keys = I.generate("zipf", 50_000, seed=11)
+    need = hs.workspace_size(0, keys.size)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev())
+    tk = to_dev(keys)
+    hs.sort_keys(tk, workspace=ws)
+    assert hs.stream_error() == 0
+    assert_equal(tk.cpu().numpy(), oracle.sort(keys)[0], "sort in a caller work space")
+    with pytest.raises(hs.HsError):
+        hs.sort_keys(tk, workspace=ws[: need // 2])
+
+
+def test_host_buffers(oracle):
+    keys = I.generate("uniform1e9", 200_000, seed=12)
+    h = keys.copy()
+    hs.sort_keys_host(h)
+    assert_equal(h, oracle.sort(keys)[0], "host-buffer sort")
+    pinned = torch.from_numpy(keys.copy()).pin_memory()
+    hs.sort_keys_host(pinned)
+    assert_equal(pinned.numpy(), oracle.sort(keys)[0], "pinned host-buffer sort")
+
+
+def test_streams_do_not_share_work_space(oracle):
+    a = I.generate("uniform31", 200_000, seed=13)
+    b = I.generate("uniform64", 150_000, seed=14)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    ta, tb = to_dev(a), to_dev(b)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        hs.sort_keys(ta, stream=s1)
+        hs.sort_keys(tb, stream=s2)
+    torch.cuda.synchronize()
+    assert_equal(ta.cpu().numpy(), oracle.sort(a)[0], "stream 1")
+    assert_equal(tb.cpu().numpy(), oracle.sort(b)[0], "stream 2")

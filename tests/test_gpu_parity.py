@@ -1,0 +1,115 @@
+"""GPU parity: every stage and the whole sort against the CPU oracle,
+element by element, bit-exact (integer work).  Sizes span several tiles and
+packet-step blocks (4096 keys each) with ragged tails, plus the edge cases:
+one key, one tile exactly, tile +- 1, empty packets, all-equal, negative
+int32 keys, the largest uint64 digit width."""
+import numpy as np
+import pytest
+
+from gpu_util import assert_equal, run
+from paper_2003_01216_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [1, 2, 100, 4095, 4096, 4097, 3 * 4096 + 123, 65536 + 17, 300_001]
+DISTS = ["uniform31", "uniform1e9", "zipf", "sorted", "reverse", "equal", "distinct16", "int32full",
+         "three_digit", "uniform32", "uniform64", "distinct2p24"]
+
+
+@pytest.mark.parametrize("dist", DISTS)
+def test_device_generator_matches_host(dist):
+    for n in (1, 1000, 100_003):
+        h = I.generate(dist, n, seed=9, stream=3)
+        d = I.device_generate(dist, n, seed=9, stream=3)
+        assert_equal(d.cpu().numpy(), h, f"device generator {dist} n={n}")
+
+
+@pytest.mark.parametrize("nb", [10, 256])
+@pytest.mark.parametrize("dist", DISTS)
+def test_partition_stage(oracle, dist, nb):
+    # the packet step alone: stable layout and packet offsets, bit-exact
+    for n in (1, 4097, 65536 + 17, 300_001):
+        keys = I.generate(dist, n, seed=1)
+        vals = I.index_values(n)
+        ek, ev, eoff = oracle.partition(keys, vals, nb)
+        gk, _, goff, st = run(keys, None, nb, stop_after=1)
+        assert st == 0
+        assert_equal(goff, eoff, f"packet offsets {dist} n={n}")
+        assert_equal(gk, ek, f"packet layout {dist} n={n}")
+        gk, gv, _, st = run(keys, vals, nb, stop_after=1)
+        assert st == 0
+        assert_equal(gk, ek, f"packet layout (pairs) {dist} n={n}")
+        assert_equal(gv, ev, f"packet layout values {dist} n={n}")
+
+
+@pytest.mark.parametrize("nb", [10, 256])
+@pytest.mark.parametrize("dist", ["uniform1e9", "zipf", "reverse", "distinct16", "uniform64", "distinct2p24"])
+def test_tilesort_stage(oracle, dist, nb):
+    # packet step + tile sort: every 4096-key tile of every packet sorted on its own
+    for n in (4097, 3 * 4096 + 123, 300_001):
+        keys = I.generate(dist, n, seed=2)
+        vals = I.index_values(n)
+        lk, lv, off = oracle.partition(keys, vals, nb)
+        ek, ev = oracle.tile_sort(lk, off, 4096, lv)
+        gk, gv, _, st = run(keys, vals, nb, stop_after=2)
+        assert st == 0
+        assert_equal(gk, ek, f"tile-sorted keys {dist} n={n}")
+        assert_equal(gv, ev, f"tile-sorted values {dist} n={n}")
+        gk, _, _, st = run(keys, None, nb, stop_after=2)
+        assert_equal(gk, ek, f"tile-sorted keys (keys only) {dist} n={n}")
+
+
+@pytest.mark.parametrize("nb", [10, 256])
+@pytest.mark.parametrize("dist", DISTS)
+def test_sort_keys(oracle, dist, nb):
+    for n in SIZES:
+        keys = I.generate(dist, n, seed=3)
+        ek, _, eoff = oracle.sort(keys, None, nb)
+        gk, _, goff, st = run(keys, None, nb)
+        assert st == 0
+        assert_equal(gk, ek, f"sorted keys {dist} n={n}")
+        assert_equal(goff, eoff, f"packet offsets {dist} n={n}")
+
+
+@pytest.mark.parametrize("nb", [10, 256])
+@pytest.mark.parametrize("dist", ["uniform31", "zipf", "equal", "distinct16", "int32full", "uniform32",
+                                  "uniform64", "distinct2p24"])
+def test_sort_pairs_stable(oracle, dist, nb):
+    for n in SIZES:
+        keys = I.generate(dist, n, seed=4)
+        vals = I.index_values(n)
+        ek, ev, _ = oracle.sort(keys, vals, nb)
+        gk, gv, _, st = run(keys, vals, nb)
+        assert st == 0
+        assert_equal(gk, ek, f"pair keys {dist} n={n}")
+        assert_equal(gv, ev, f"pair values (stable order) {dist} n={n}")
+
+
+def test_config1_plain_keys(oracle):
+    # 1,048,576 int32 keys uniform in [0, 10^9) from seed 0: D = 9, packet = key / 10^8
+    keys = I.generate("uniform1e9", 1 << 20, seed=0)
+    ek, _, eoff = oracle.sort(keys, None, 10)
+    gk, _, goff, st = run(keys)
+    assert st == 0
+    assert_equal(gk, ek, "config 1 sorted keys")
+    assert_equal(goff, eoff, "config 1 packet offsets")
+    counts = np.diff(goff.astype(np.int64))
+    assert counts.size == 10 and np.all(np.abs(counts - (1 << 20) / 10) < 5 * 310)
+
+
+def test_special_values(oracle):
+    for dt in (np.int32, np.uint32, np.uint64):
+        info = np.iinfo(dt)
+        base = np.array([info.max, info.min, 0, 9, 10, 99, 100, info.max, 1], dtype=dt)
+        keys = np.tile(base, 1000)
+        for nb in (10, 256):
+            ek, _, eoff = oracle.sort(keys, None, nb)
+            gk, _, goff, st = run(keys, None, nb)
+            assert st == 0
+            assert_equal(gk, ek, f"special values {dt}")
+            assert_equal(goff, eoff, f"special values offsets {dt}")
+
+
+def test_empty_input():
+    gk, _, goff, st = run(np.zeros(0, np.int32))
+    assert gk.size == 0 and st == 0 and np.all(goff == 0)
