@@ -158,7 +158,6 @@ struct Tables {
   uint64_t* pkt_off;      // nseg * NB + 1 absolute packet starts
   uint32_t* unit_prefix;  // nseg * NB + 1: first tile of each packet (tile = merge block)
   uint64_t* status;       // total blocks * NB look-back words
-  uint32_t* corank;       // tiles + 1: merge-path split of each merge block
   uint32_t* counters;     // [0] block ticket, [1..] spare
   uint32_t* err;          // device error word
 };

@@ -22,7 +22,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
   size_t keys_w, vals_w, seg_off, blk_prefix, hist, seg_neg, seg_class, seg_flip, pkt_off, unit_prefix, status,
-      corank, counters, total;
+      recs, counters, total;
   size_t hist_words, status_words;
   uint32_t max_blocks, max_units, npk;
 };
@@ -52,7 +52,7 @@ inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg
   L.unit_prefix = take((L.npk + 1) * 4);
   L.status_words = static_cast<size_t>(L.max_blocks) * nb;
   L.status = take(L.status_words * 8);
-  L.corank = take((static_cast<size_t>(L.max_units) + 1) * 4);
+  L.recs = take((static_cast<size_t>(L.max_units) + 1) * sizeof(MergeRec));
   L.counters = take(16 * 4);
   L.total = off;
   return L;
@@ -69,7 +69,6 @@ inline Tables make_tables(char* base, const Layout& L, uint32_t* err) {
   t.pkt_off = reinterpret_cast<uint64_t*>(base + L.pkt_off);
   t.unit_prefix = reinterpret_cast<uint32_t*>(base + L.unit_prefix);
   t.status = reinterpret_cast<uint64_t*>(base + L.status);
-  t.corank = reinterpret_cast<uint32_t*>(base + L.corank);
   t.counters = reinterpret_cast<uint32_t*>(base + L.counters);
   t.err = err;
   return t;
@@ -100,6 +99,10 @@ inline size_t scatter_smem() {
 template <class K, bool HAS_V>
 inline size_t sort_smem() {
   return padded(kTile) * sizeof(K) + (HAS_V ? padded(kTile) * 4 : 0);
+}
+template <class K, bool HAS_V>
+inline size_t merge_smem() {  // two pipeline stages
+  return 2 * sort_smem<K, HAS_V>();
 }
 
 template <class Kern>
@@ -187,18 +190,19 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       if (HAS_V) HS_TRY(lc.copy("copy_back_v", vals, vw, n * 4));
     } else {
       static int mgrid = 0, cgrid = 0;
-      const size_t smem = sort_smem<K, HAS_V>();
+      const size_t smem = merge_smem<K, HAS_V>();
       auto mk = k_merge<K, HAS_V, kBlock, kIpt>;
       auto ck = k_corank<K, kTile>;
       if (!mgrid) mgrid = persistent_grid(mk, kBlock, smem);
       if (!cgrid) cgrid = persistent_grid(ck, 256, 0);
+      MergeRec* recs = reinterpret_cast<MergeRec*>(ws + L.recs);
       const int P = worst_passes(n);
       for (int r = 1; r <= P; ++r) {
         lc.begin("corank");
-        ck<<<cgrid, 256, 0, st>>>(keys, kw, L.npk, r, tb);
+        ck<<<cgrid, 256, 0, st>>>(keys, kw, recs, L.npk, r, tb);
         HS_TRY(lc.end());
         lc.begin("merge");
-        mk<<<mgrid, kBlock, smem, st>>>(keys, vals, kw, vw, L.npk, r, tb);
+        mk<<<mgrid, kBlock, smem, st>>>(keys, vals, kw, vw, recs, L.npk, tb);
         HS_TRY(lc.end());
       }
     }

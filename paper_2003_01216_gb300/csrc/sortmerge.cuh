@@ -248,75 +248,150 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
 }
 
 // ---------------------------------------------------------------------------
-// k_corank: merge-path split of the first output of every merge block of
-// pass r, by binary search in global memory.
+// Merge pass r, step 1 -- k_corank: for every merge block, the split of its
+// first and of its one-past-last output between the two runs it merges (the
+// merge path co-ranks), packed into a record the merge kernel reads once.
+// Each thread runs both searches interleaved as 8-ary searches (7 independent
+// probes per round), so a run of 2^27 keys takes 9 dependent rounds.
 // ---------------------------------------------------------------------------
+struct MergeRec {
+  uint64_t a;    // absolute index of the block's first A item; bit 63: source buffer is W
+  uint64_t b;    // absolute index of the block's first B item
+  uint64_t out;  // absolute index of the block's first output
+  uint32_t la;   // A items merged by the block
+  uint32_t lb;   // B items merged by the block (la + lb = outputs; 0 = nothing to do)
+};
+constexpr uint64_t kSrcW = 1ull << 63;
+
+// Number of A items among the first `diag` outputs of merging A[0, la) and
+// B[0, lb) with A first on ties; two diagonals at once.
+template <class K>
+__device__ __forceinline__ void corank2(const K* __restrict__ A, uint32_t la, const K* __restrict__ B, uint32_t lb,
+                                        uint32_t d0, uint32_t d1, uint32_t& r0, uint32_t& r1) {
+  uint32_t lo0 = d0 > lb ? d0 - lb : 0, hi0 = min(d0, la);
+  uint32_t lo1 = d1 > lb ? d1 - lb : 0, hi1 = min(d1, la);
+  // g(i) = A[i] <= B[d - 1 - i] is true for i below the answer, false from it on
+  while (hi0 > lo0 || hi1 > lo1) {
+    const uint32_t st0 = (hi0 - lo0 + 7) >> 3, st1 = (hi1 - lo1 + 7) >> 3;
+    uint32_t t0 = 0, t1 = 0;
+#pragma unroll
+    for (int j = 1; j <= 8; ++j) {
+      const uint32_t p0 = lo0 + (j - 1) * st0, p1 = lo1 + (j - 1) * st1;
+      if (hi0 > lo0 && p0 < hi0 && !(B[d0 - 1 - p0] < A[p0])) ++t0;
+      if (hi1 > lo1 && p1 < hi1 && !(B[d1 - 1 - p1] < A[p1])) ++t1;
+    }
+    // t probes true: the answer lies in (lo + (t-1)*st, lo + t*st]
+    if (hi0 > lo0) {
+      if (t0 == 0) hi0 = lo0;
+      else {
+        const uint32_t nl = lo0 + (t0 - 1) * st0 + 1;
+        hi0 = min(hi0, lo0 + t0 * st0);
+        lo0 = min(nl, hi0);
+      }
+    }
+    if (hi1 > lo1) {
+      if (t1 == 0) hi1 = lo1;
+      else {
+        const uint32_t nl = lo1 + (t1 - 1) * st1 + 1;
+        hi1 = min(hi1, lo1 + t1 * st1);
+        lo1 = min(nl, hi1);
+      }
+    }
+  }
+  r0 = lo0;
+  r1 = lo1;
+}
+
 template <class K, int TILE>
-__global__ void k_corank(const K* __restrict__ ku, const K* __restrict__ kw, uint32_t npk, int r, Tables tb) {
+__global__ void k_corank(const K* __restrict__ ku, const K* __restrict__ kw, MergeRec* __restrict__ recs,
+                         uint32_t npk, int r, Tables tb) {
   const uint32_t total = tb.unit_prefix[npk];
   for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
     MergeGeom g;
-    if (!merge_geom<TILE>(tb, npk, u, r, g)) continue;
-    const K* src = ((g.passes - r + 1) & 1) ? kw : ku;  // buffer holding pass r-1
-    const K* A = src + g.pstart + g.a_start;
-    const K* B = A + g.a_len;
-    const uint32_t diag = g.diag0;
-    uint32_t lo = diag > g.b_len ? diag - g.b_len : 0;
-    uint32_t hi = min(diag, g.a_len);
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (!(B[diag - 1 - mid] < A[mid])) lo = mid + 1; else hi = mid;
+    MergeRec rec{0, 0, 0, 0, 0};
+    if (merge_geom<TILE>(tb, npk, u, r, g)) {
+      const bool srcw = ((g.passes - r + 1) & 1) != 0;  // the buffer holding pass r-1
+      const K* A = (srcw ? kw : ku) + g.pstart + g.a_start;
+      const K* B = A + g.a_len;
+      uint32_t i0, i1;
+      corank2(A, g.a_len, B, g.b_len, g.diag0, g.diag0 + g.cnt, i0, i1);
+      const uint64_t abs_a = g.pstart + g.a_start;
+      rec.a = (abs_a + i0) | (srcw ? kSrcW : 0ull);
+      rec.b = abs_a + g.a_len + (g.diag0 - i0);
+      rec.out = abs_a + g.diag0;
+      rec.la = i1 - i0;
+      rec.lb = g.cnt - rec.la;
     }
-    tb.corank[u] = lo;
+    recs[u] = rec;
   }
 }
 
 // ---------------------------------------------------------------------------
-// k_merge: merge pass r.
+// Merge pass r, step 2 -- k_merge: persistent CTAs; each walks merge blocks
+// blockIdx.x, +gridDim.x, ...  A two-stage pipeline of asynchronous copies
+// (cp.async, global -> padded shared memory) loads block k+1's A and B items
+// while block k is merged; block k+2's record is fetched one block ahead.
 // ---------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 template <class K, bool HAS_V, int BLOCK, int IPT>
-__global__ void __launch_bounds__(BLOCK) k_merge(K* ku, uint32_t* vu, K* kw, uint32_t* vw, uint32_t npk, int r,
-                                                  Tables tb) {
+__device__ __forceinline__ void merge_issue(const MergeRec& rec, K* sk, uint32_t* sv, const K* ku, const uint32_t* vu,
+                                            const K* kw, const uint32_t* vw) {
+  const bool srcw = (rec.a & kSrcW) != 0;
+  const K* ks = srcw ? kw : ku;
+  const uint32_t* vs = srcw ? vw : vu;
+  const uint64_t a = rec.a & ~kSrcW;
+  const int la = static_cast<int>(rec.la), cnt = static_cast<int>(rec.la + rec.lb);
+#pragma unroll
+  for (int c = 0; c < IPT; ++c) {
+    const int e = c * BLOCK + static_cast<int>(threadIdx.x);
+    if (e < cnt) {
+      const uint64_t gi = (e < la) ? a + e : rec.b + (e - la);
+      cp_async<sizeof(K)>(&sk[pad(e)], ks + gi);
+      if constexpr (HAS_V) cp_async<4>(&sv[pad(e)], vs + gi);
+    }
+  }
+}
+
+template <class K, bool HAS_V, int BLOCK, int IPT>
+__global__ void __launch_bounds__(BLOCK, HAS_V ? 2 : 4) k_merge(K* ku, uint32_t* vu, K* kw, uint32_t* vw,
+                                                  const MergeRec* __restrict__ recs, uint32_t npk, Tables tb) {
   constexpr int TILE = BLOCK * IPT;
+  constexpr int SP = padded(TILE);
   extern __shared__ __align__(16) unsigned char s_raw[];
-  K* sk = reinterpret_cast<K*>(s_raw);
-  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + padded(TILE));
+  K* skb = reinterpret_cast<K*>(s_raw);                         // 2 stages of SP keys
+  uint32_t* svb = reinterpret_cast<uint32_t*>(skb + 2 * SP);    // 2 stages of SP values (pairs)
   const int tid = threadIdx.x;
   const uint32_t total = tb.unit_prefix[npk];
-
-  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
-    MergeGeom g;
-    if (!merge_geom<TILE>(tb, npk, u, r, g)) continue;  // block-uniform
-    const bool src_w = ((g.passes - r + 1) & 1) != 0;
-    const K* ks = src_w ? kw : ku;
-    const uint32_t* vs = src_w ? vw : vu;
-    K* kd = src_w ? ku : kw;
-    uint32_t* vd = src_w ? vu : vw;
-    const uint32_t i0 = tb.corank[u];
-    const uint32_t i1 = g.last_in_pair ? g.a_len : tb.corank[u + 1];
-    const uint32_t j0 = g.diag0 - i0;
-    const int la = static_cast<int>(i1 - i0), cnt = static_cast<int>(g.cnt);
-    const K* A = ks + g.pstart + g.a_start;
-    const K* B = A + g.a_len;
-    const uint32_t* VA = vs + g.pstart + g.a_start;
-    const uint32_t* VB = VA + g.a_len;
-
-#pragma unroll
-    for (int c = 0; c < IPT; ++c) {
-      const int e = c * BLOCK + tid;
-      if (e < cnt) {
-        const bool fa = e < la;
-        sk[pad(e)] = fa ? A[i0 + e] : B[j0 + (e - la)];
-        if constexpr (HAS_V) sv[pad(e)] = fa ? VA[i0 + e] : VB[j0 + (e - la)];
-      }
-    }
-    __syncthreads();
+  const uint32_t G = gridDim.x;
+  uint32_t u = blockIdx.x;
+  if (u >= total) return;
+  const MergeRec none{0, 0, 0, 0, 0};
+  MergeRec cur = recs[u];
+  MergeRec nxt = (u + G < total) ? recs[u + G] : none;
+  merge_issue<K, HAS_V, BLOCK, IPT>(cur, skb, svb, ku, vu, kw, vw);
+  cp_async_commit();
+  int s = 0;
+  for (; u < total; u += G) {
+    const MergeRec nn = (u + 2 * G < total) ? recs[u + 2 * G] : none;
+    merge_issue<K, HAS_V, BLOCK, IPT>(nxt, skb + (s ^ 1) * SP, svb + (s ^ 1) * SP, ku, vu, kw, vw);
+    cp_async_commit();
+    cp_async_wait_1();  // this thread's copies for block `cur` have landed
+    __syncthreads();    // ... and every other thread's
+    K* sk = skb + s * SP;
+    uint32_t* sv = svb + s * SP;
+    const int la = static_cast<int>(cur.la), cnt = static_cast<int>(cur.la + cur.lb);
     K k[IPT];
     int idx[IPT];
     const int d = tid * IPT;
     if (d < cnt) {
-      const int lb = cnt - la;
-      const int i = corank_smem(sk, 0, la, la, lb, d);
+      const int i = corank_smem(sk, 0, la, la, cnt - la, d);
       serial_merge<K, IPT>(sk, i, la, la + d - i, cnt, min(IPT, cnt - d), k, idx);
     }
     uint32_t v[IPT];
@@ -334,8 +409,9 @@ __global__ void __launch_bounds__(BLOCK) k_merge(K* ku, uint32_t* vu, K* kw, uin
       }
     }
     __syncthreads();
-    K* out = kd + g.pstart + g.a_start + g.diag0;
-    uint32_t* vout = vd + g.pstart + g.a_start + g.diag0;
+    const bool srcw = (cur.a & kSrcW) != 0;
+    K* out = (srcw ? ku : kw) + cur.out;
+    uint32_t* vout = (srcw ? vu : vw) + cur.out;
 #pragma unroll
     for (int c = 0; c < IPT; ++c) {
       const int e = c * BLOCK + tid;
@@ -344,7 +420,10 @@ __global__ void __launch_bounds__(BLOCK) k_merge(K* ku, uint32_t* vu, K* kw, uin
         if constexpr (HAS_V) vout[e] = sv[pad(e)];
       }
     }
-    __syncthreads();
+    __syncthreads();  // stage s is free for block k+2's copies
+    cur = nxt;
+    nxt = nn;
+    s ^= 1;
   }
 }
 
