@@ -123,6 +123,29 @@ hs_status hs_sort_batch(hs_dtype dtype, void* d_keys, uint32_t* d_vals, const ui
  */
 hs_status hs_sort_keys_host(hs_dtype dtype, void* h_keys, size_t n, const hs_opts* opts, void* stream);
 
+/*
+ * hs_sort_keys_noalloc -- hs_sort_keys for callers that cannot allocate device
+ * memory (the paper has no counterpart: this is an interface for such callers,
+ * e.g. code inside a stream capture that must hold no allocation, or a host
+ * framework that owns every device allocation).  The scratch lives in a
+ * fixed 16 MiB device array inside this library; every GPU that loads the
+ * library holds it until the process exits.  No cudaMalloc, cudaFree or other
+ * allocating call is made.
+ *   dtype, d_keys, n, stream  as hs_sort_keys (sorted in place)
+ *   partition  10 or 256 (0 = 10)
+ * Limits and rules:
+ *   - n <= 1,048,576 keys, else HS_ERR_INVALID (hs_last_error says why);
+ *   - per-kernel timing (hs_timing_enable) must be off, else HS_ERR_INVALID;
+ *   - the first call on a device sets up that device (looks up the device
+ *     address of the scratch array with that device current); make that first
+ *     call before any stream capture;
+ *   - every call shares the one scratch array, which keeps the previous call's
+ *     contents (the sort clears what it needs): calls whose work overlaps on
+ *     the GPU (different streams, or different host threads) race and must be
+ *     ordered by the caller.
+ */
+hs_status hs_sort_keys_noalloc(hs_dtype dtype, void* d_keys, size_t n, int partition, void* stream);
+
 /* Work space needed by one call (bytes).  nseg = 1 and d_offsets unused for
  * the plain sorts; has_vals = 1 for pairs. */
 hs_status hs_workspace_size(hs_dtype dtype, size_t n, int has_vals, size_t nseg,

@@ -20,6 +20,7 @@ EXPORTS = [
     "hs_sort_keys", "hs_sort_pairs", "hs_sort_batch", "hs_sort_keys_host", "hs_workspace_size",
     "hs_workspace_reserve", "hs_workspace_release", "hs_stream_error", "hs_plan_describe",
     "hs_timing_enable", "hs_timing_read", "hs_kernel_launches", "hs_status_string", "hs_last_error",
+    "hs_sort_keys_noalloc",
 ]
 
 
@@ -73,6 +74,7 @@ def lib() -> ctypes.CDLL:
         L.hs_sort_pairs.argtypes = [i, p, p, sz, i, p, p]
         L.hs_sort_batch.argtypes = [i, p, p, p, sz, sz, p, p]
         L.hs_sort_keys_host.argtypes = [i, p, sz, p, p]
+        L.hs_sort_keys_noalloc.argtypes = [i, p, sz, i, p]
         L.hs_workspace_size.argtypes = [i, sz, i, sz, p, p]
         L.hs_workspace_reserve.argtypes = [sz, p]
         L.hs_workspace_release.argtypes = []

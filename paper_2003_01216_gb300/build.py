@@ -22,7 +22,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxe
          "-I", os.path.join(ROOT, "include")]
 
 LIBS = {
-    "libhsort.so": ["hsort_abi.cu", "sort_i32.cu", "sort_u32.cu", "sort_u64.cu"],
+    "libhsort.so": ["hsort_abi.cu", "hsort_noalloc.cu", "sort_i32.cu", "sort_u32.cu", "sort_u64.cu"],
     "libhsgen.so": ["gen.cu"],
 }
 HEADERS = ["common.cuh", "partition.cuh", "sortmerge.cuh", "driver.cuh", "runtime.h"]

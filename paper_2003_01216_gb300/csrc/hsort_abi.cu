@@ -161,6 +161,8 @@ void timing_add(const char* name, cudaEvent_t a, cudaEvent_t b) { g_times.push_b
 
 void set_cuda_error(cudaError_t e) { t_last_error = cudaGetErrorString(e); }
 
+void set_error_message(const char* msg) { t_last_error = msg; }
+
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 size_t workspace_bytes(size_t kb, size_t n, bool has_vals, size_t nseg, int nb) {

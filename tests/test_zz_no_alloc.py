@@ -1,0 +1,59 @@
+"""hs_sort_keys_noalloc: the keys-only sort for callers that cannot allocate
+device memory (its scratch is a fixed array inside the library).  Called
+through the C ABI and compared with hs_sort_keys, bit for bit, on two calls in
+a row.  Collected last, so a run stopping at its first failure has already run
+every other test; it also passes alone in a fresh process."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2003_01216_gb300 as hs
+from paper_2003_01216_gb300 import _native as N
+from paper_2003_01216_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+MAX_KEYS = 1 << 20
+
+
+def _noalloc(t, partition=10):
+    stream = torch.cuda.current_stream().cuda_stream
+    return N.lib().hs_sort_keys_noalloc(hs.dtype_code(t), t.data_ptr(), t.numel(), partition, stream)
+
+
+@pytest.mark.parametrize("dist,partition", [("uniform1e9", 10), ("int32full", 256), ("uniform64", 10),
+                                            ("uniform32", 10)])
+def test_noalloc_matches_sort_keys_twice(dist, partition):
+    hs.timing_enable(False)
+    dev = torch.device("cuda", 0)
+    for call, (n, seed) in enumerate([(MAX_KEYS, 21), (300_001, 22)]):
+        keys = I.generate(dist, n, seed=seed)
+        ref = torch.from_numpy(keys).to(dev)
+        hs.sort_keys(ref, partition=partition)
+        got = torch.from_numpy(keys).to(dev)
+        assert _noalloc(got, partition) == N.HS_OK, f"call {call}"
+        assert hs.stream_error() == 0
+        assert np.array_equal(got.cpu().numpy(), ref.cpu().numpy()), f"call {call}: differs from hs_sort_keys"
+
+
+def test_noalloc_rejects_oversize_and_timing():
+    dev = torch.device("cuda", 0)
+    big = torch.zeros(MAX_KEYS + 1, dtype=torch.int32, device=dev)
+    assert _noalloc(big) == N.HS_ERR_INVALID
+    assert b"exceeds the maximum" in N.lib().hs_last_error()
+    small = torch.arange(1000, 0, -1, dtype=torch.int32, device=dev)
+    hs.timing_enable(True)
+    try:
+        assert _noalloc(small) == N.HS_ERR_INVALID
+    finally:
+        hs.timing_enable(False)
+    assert _noalloc(small) == N.HS_OK
+    assert hs.stream_error() == 0
+    assert torch.equal(small.cpu(), torch.arange(1, 1001, dtype=torch.int32))
+
+
+def test_noalloc_symbol_declared():
+    assert hasattr(N.lib(), "hs_sort_keys_noalloc")
+    assert ctypes.sizeof(ctypes.c_void_p) == 8
