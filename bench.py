@@ -213,10 +213,12 @@ def run_reference(args, rank, world):
 
 
 def workload_config(args, dist, n, has_vals):
+    import paper_2003_01216_gb300 as hs
+    tile = hs.plan(0, n)["tile"]
     return {"workload": f"{args.workload}_{n}_{dist}_{args.partition}pkt", "n": n, "dist": dist,
             "key_dtype": "uint64" if dist in ("uniform64", "distinct2p24") else "int32",
             "values": "uint32 input index" if has_vals else None, "partition": args.partition,
-            "tile": 4096, "fan_in": 2, "seed": 0,
+            "tile": tile, "fan_in": 2, "seed": 0,
             "l2": "inputs larger than L2 (>= 1 GiB vs 129 MB); a 1 GiB restore copy between timed steps"}
 
 

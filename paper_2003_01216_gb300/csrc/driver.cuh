@@ -15,7 +15,7 @@ namespace hs {
 
 // Fixed shapes of this build.
 constexpr int kBlock = 256;     // threads per CTA of every heavy kernel
-constexpr int kIpt = 16;        // items per thread
+constexpr int kIpt = 15;        // items per thread (odd: blocked shared-memory access is conflict-free)
 constexpr int kTile = kBlock * kIpt;  // keys per tile sort / merge block / packet-step block
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -97,12 +97,12 @@ inline size_t scatter_smem() {
   return b;
 }
 template <class K, bool HAS_V>
-inline size_t sort_smem() {
-  return padded(kTile) * sizeof(K) + (HAS_V ? padded(kTile) * 4 : 0);
+inline size_t sort_smem() {  // one region of keys (and values)
+  return merge_stage_bytes<K, HAS_V>(kTile);
 }
 template <class K, bool HAS_V>
 inline size_t merge_smem() {  // two pipeline stages
-  return 2 * sort_smem<K, HAS_V>();
+  return 2 * merge_stage_bytes<K, HAS_V>(kTile);
 }
 
 template <class Kern>

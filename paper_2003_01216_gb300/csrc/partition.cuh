@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(BLOCK) k_scatter(const K* __restrict__ keys_in
   constexpr int NW = BLOCK / kWarp;
   constexpr int TILE = BLOCK * IPT;
   constexpr int NBX = NB + 1;  // + a dummy packet for lanes past the end
-  extern __shared__ __align__(16) unsigned char s_raw[];
+  extern __shared__ __align__(128) unsigned char s_raw[];
   K* s_keys = reinterpret_cast<K*>(s_raw);                                    // TILE
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + TILE);             // TILE (pairs)
   uint32_t* s_wc = s_vals + (HAS_V ? TILE : 0);                              // NW * NBX warp counts

@@ -65,11 +65,17 @@ def test_host_side_rejections():
     assert lib.hs_sort_keys_host(0, None, 5, None, None) == N.HS_ERR_INVALID
 
 
-@pytest.mark.parametrize("n,passes", [(1, 0), (4096, 0), (4097, 1), (1 << 20, 8), (1 << 28, 16)])
-def test_plan_describe(n, passes):
+@pytest.mark.parametrize("n", [1, 3839, 3840, 3841, 1 << 20, 1 << 28])
+def test_plan_describe(n):
+    import math
+
     import paper_2003_01216_gb300 as hs
     p = hs.plan(N.HS_INT32, n)
-    assert p["tile"] == 4096 and p["merge_passes"] == passes
+    tile = p["tile"]
+    assert tile == 256 * 15
+    tiles = -(-n // tile)
+    passes = 0 if tiles <= 1 else math.ceil(math.log2(tiles))
+    assert p["merge_passes"] == passes
     # seg_plan, 2 histogram passes (int32), finalize, scan, scatter, tile sort, 2 per merge pass
     assert p["launches"] == 7 + 2 * passes
     assert hs.plan(N.HS_UINT64, n)["launches"] == 6 + 2 * passes

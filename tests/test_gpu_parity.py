@@ -1,17 +1,19 @@
 """GPU parity: every stage and the whole sort against the CPU oracle,
 element by element, bit-exact (integer work).  Sizes span several tiles and
-packet-step blocks (4096 keys each) with ragged tails, plus the edge cases:
+packet-step blocks (TILE keys each) with ragged tails, plus the edge cases:
 one key, one tile exactly, tile +- 1, empty packets, all-equal, negative
 int32 keys, the largest uint64 digit width."""
 import numpy as np
 import pytest
 
+import paper_2003_01216_gb300 as hs
 from gpu_util import assert_equal, run
 from paper_2003_01216_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [1, 2, 100, 4095, 4096, 4097, 3 * 4096 + 123, 65536 + 17, 300_001]
+TILE = hs.plan(0, 1 << 20)["tile"]  # keys per tile, merge block and packet-step block
+SIZES = [1, 2, 100, TILE - 1, TILE, TILE + 1, 3 * TILE + 123, 65536 + 17, 300_001]
 DISTS = ["uniform31", "uniform1e9", "zipf", "sorted", "reverse", "equal", "distinct16", "int32full",
          "three_digit", "uniform32", "uniform64", "distinct2p24"]
 
@@ -28,7 +30,7 @@ def test_device_generator_matches_host(dist):
 @pytest.mark.parametrize("dist", DISTS)
 def test_partition_stage(oracle, dist, nb):
     # the packet step alone: stable layout and packet offsets, bit-exact
-    for n in (1, 4097, 65536 + 17, 300_001):
+    for n in (1, TILE + 1, 65536 + 17, 300_001):
         keys = I.generate(dist, n, seed=1)
         vals = I.index_values(n)
         ek, ev, eoff = oracle.partition(keys, vals, nb)
@@ -45,12 +47,12 @@ def test_partition_stage(oracle, dist, nb):
 @pytest.mark.parametrize("nb", [10, 256])
 @pytest.mark.parametrize("dist", ["uniform1e9", "zipf", "reverse", "distinct16", "uniform64", "distinct2p24"])
 def test_tilesort_stage(oracle, dist, nb):
-    # packet step + tile sort: every 4096-key tile of every packet sorted on its own
-    for n in (4097, 3 * 4096 + 123, 300_001):
+    # packet step + tile sort: every tile of every packet sorted on its own
+    for n in (TILE + 1, 3 * TILE + 123, 300_001):
         keys = I.generate(dist, n, seed=2)
         vals = I.index_values(n)
         lk, lv, off = oracle.partition(keys, vals, nb)
-        ek, ev = oracle.tile_sort(lk, off, 4096, lv)
+        ek, ev = oracle.tile_sort(lk, off, TILE, lv)
         gk, gv, _, st = run(keys, vals, nb, stop_after=2)
         assert st == 0
         assert_equal(gk, ek, f"tile-sorted keys {dist} n={n}")
