@@ -151,14 +151,17 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 struct Tables {
   uint64_t* seg_off;      // nseg + 1 absolute segment starts
   uint32_t* blk_prefix;   // nseg + 1: first packet-step block of each segment
-  uint32_t* hist;         // nseg * 2 * NCLASS * NB class histograms (identity image, flipped image)
+  uint32_t* cls_raw;      // blocks: class of each block's largest key image
+  uint32_t* cnt_raw;      // blocks * NB: each block's packet counts under its own class
+  uint32_t* flat;         // blocks * NB: counts under the segment class in (segment, packet, block)
+                          // order, then scanned in place into absolute first positions
+  uint32_t* scan_part;    // scan partials
   uint32_t* seg_neg;      // nseg: segment holds a negative int32 key
+  uint32_t* seg_cmax;     // nseg * 2: largest block class (identity image, flipped image)
   uint32_t* seg_class;    // nseg: final class (D or B) of the segment
   uint32_t* seg_flip;     // nseg: sign flip in use
   uint64_t* pkt_off;      // nseg * NB + 1 absolute packet starts
   uint32_t* unit_prefix;  // nseg * NB + 1: first tile of each packet (tile = merge block)
-  uint64_t* status;       // total blocks * NB look-back words
-  uint32_t* counters;     // [0] block ticket, [1..] spare
   uint32_t* err;          // device error word
 };
 

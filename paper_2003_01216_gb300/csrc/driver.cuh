@@ -21,15 +21,13 @@ constexpr int kTile = kBlock * kIpt;  // keys per tile sort / merge block / pack
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-  size_t keys_w, vals_w, seg_off, blk_prefix, hist, seg_neg, seg_class, seg_flip, pkt_off, unit_prefix, status,
-      recs, counters, total;
-  size_t hist_words, status_words;
+  size_t keys_w, vals_w, seg_off, blk_prefix, cls_raw, cnt_raw, flat, scan_part, seg_neg, seg_cmax, seg_class,
+      seg_flip, pkt_off, unit_prefix, recs, total;
   uint32_t max_blocks, max_units, npk;
 };
 
 inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg, int nb) {
   Layout L{};
-  const int ncls = (nb == 10) ? kDecClasses : kBinClasses;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -43,17 +41,17 @@ inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg
   L.vals_w = take(has_vals ? n * 4 + 16 : 0);
   L.seg_off = take((nseg + 1) * 8);
   L.blk_prefix = take((nseg + 1) * 4);
-  L.hist_words = nseg * 2 * ncls * nb;
-  L.hist = take(L.hist_words * 4);
+  L.cls_raw = take(static_cast<size_t>(L.max_blocks) * 4);
+  L.cnt_raw = take(static_cast<size_t>(L.max_blocks) * nb * 4);
+  L.flat = take(static_cast<size_t>(L.max_blocks) * nb * 4);
+  L.scan_part = take(kScanChunks * 4);
   L.seg_neg = take(nseg * 4);
+  L.seg_cmax = take(nseg * 2 * 4);
   L.seg_class = take(nseg * 4);
   L.seg_flip = take(nseg * 4);
   L.pkt_off = take((L.npk + 1) * 8);
   L.unit_prefix = take((L.npk + 1) * 4);
-  L.status_words = static_cast<size_t>(L.max_blocks) * nb;
-  L.status = take(L.status_words * 8);
   L.recs = take((static_cast<size_t>(L.max_units) + 1) * sizeof(MergeRec));
-  L.counters = take(16 * 4);
   L.total = off;
   return L;
 }
@@ -62,14 +60,16 @@ inline Tables make_tables(char* base, const Layout& L, uint32_t* err) {
   Tables t;
   t.seg_off = reinterpret_cast<uint64_t*>(base + L.seg_off);
   t.blk_prefix = reinterpret_cast<uint32_t*>(base + L.blk_prefix);
-  t.hist = reinterpret_cast<uint32_t*>(base + L.hist);
+  t.cls_raw = reinterpret_cast<uint32_t*>(base + L.cls_raw);
+  t.cnt_raw = reinterpret_cast<uint32_t*>(base + L.cnt_raw);
+  t.flat = reinterpret_cast<uint32_t*>(base + L.flat);
+  t.scan_part = reinterpret_cast<uint32_t*>(base + L.scan_part);
   t.seg_neg = reinterpret_cast<uint32_t*>(base + L.seg_neg);
+  t.seg_cmax = reinterpret_cast<uint32_t*>(base + L.seg_cmax);
   t.seg_class = reinterpret_cast<uint32_t*>(base + L.seg_class);
   t.seg_flip = reinterpret_cast<uint32_t*>(base + L.seg_flip);
   t.pkt_off = reinterpret_cast<uint64_t*>(base + L.pkt_off);
   t.unit_prefix = reinterpret_cast<uint32_t*>(base + L.unit_prefix);
-  t.status = reinterpret_cast<uint64_t*>(base + L.status);
-  t.counters = reinterpret_cast<uint32_t*>(base + L.counters);
   t.err = err;
   return t;
 }
@@ -89,10 +89,8 @@ inline size_t scatter_smem() {
   b += kTile * sizeof(K);
   b += HAS_V ? kTile * 4 : 0;
   b += NW * (NB + 1) * 4;
-  b += ((NB + 1) & ~1) * 4;
   b += ((NB + 2) & ~1) * 4;
-  b = align_up(b, 8);
-  b += NB * 8;
+  b += ((NB + 1) & ~1) * 4;
   b += kTile * 2;
   return b;
 }
@@ -127,14 +125,11 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
   K* kw = reinterpret_cast<K*>(ws + L.keys_w);
   uint32_t* vw = HAS_V ? reinterpret_cast<uint32_t*>(ws + L.vals_w) : nullptr;
   const uint32_t nseg32 = static_cast<uint32_t>(nseg);
-  const int ncls = (NB == 10) ? kDecClasses : kBinClasses;
   Launcher lc(st);
 
-  // zero the accumulators, flags and look-back words
-  HS_TRY(lc.memset("zero_hist", tb.hist, 0, L.hist_words * 4));
-  HS_TRY(lc.memset("zero_segneg", tb.seg_neg, 0, nseg * 4));
-  HS_TRY(lc.memset("zero_status", tb.status, 0, L.status_words * 8));
-  HS_TRY(lc.memset("zero_counters", tb.counters, 0, 16 * 4));
+  // zero the per-segment flags and maxima
+  HS_TRY(lc.memset("zero_seg", tb.seg_neg, 0, nseg * 4));
+  HS_TRY(lc.memset("zero_cmax", tb.seg_cmax, 0, nseg * 2 * 4));
 
   lc.begin("seg_plan");
   k_seg_plan<<<1, 1024, 0, st>>>(offs, nseg32, n, kTile, tb);
@@ -142,18 +137,42 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
 
   {
     static int grid = 0;
-    const size_t smem = static_cast<size_t>(ncls) * NB * 4;
     auto kern = k_hist<K, NB, kBlock, kIpt>;
-    if (!grid) grid = persistent_grid(kern, kBlock, smem);
+    if (!grid) grid = persistent_grid(kern, kBlock, 0);
     for (int img = 0; img < (std::is_same<K, int32_t>::value ? 2 : 1); ++img) {
       lc.begin(img ? "hist_flip" : "hist");
-      kern<<<grid, kBlock, smem, st>>>(keys, nseg32, kTile, img, tb);
+      kern<<<grid, kBlock, 0, st>>>(keys, nseg32, kTile, img, tb);
       HS_TRY(lc.end());
     }
   }
   lc.begin("finalize");
-  k_finalize<NB><<<(nseg32 + kFinWarps - 1) / kFinWarps, kFinWarps * 32, 0, st>>>(nseg32, kTile, tb);
+  k_finalize<NB><<<(nseg32 + 255) / 256, 256, 0, st>>>(nseg32, tb);
   HS_TRY(lc.end());
+  {
+    static int grid = 0;
+    if (!grid) grid = persistent_grid(k_fold<NB>, 256, 0);
+    lc.begin("fold");
+    k_fold<NB><<<grid, 256, 0, st>>>(nseg32, tb);
+    HS_TRY(lc.end());
+  }
+  // exclusive scan of the (segment, packet, block) counts: absolute positions
+  const uint32_t* m_ptr = tb.blk_prefix + nseg;  // total blocks (device)
+  lc.begin("scan_reduce");
+  k_scan_reduce<<<kScanChunks, kScanBlock, 0, st>>>(tb.flat, m_ptr, NB, tb.scan_part);
+  HS_TRY(lc.end());
+  lc.begin("scan_partials");
+  k_scan_partials<<<1, kScanBlock, 0, st>>>(tb.scan_part);
+  HS_TRY(lc.end());
+  lc.begin("scan_down");
+  k_scan_down<<<kScanChunks, kScanBlock, 0, st>>>(tb.flat, m_ptr, NB, tb.scan_part);
+  HS_TRY(lc.end());
+  {
+    static int grid = 0;
+    if (!grid) grid = persistent_grid(k_pkt<NB>, 256, 0);
+    lc.begin("pkt");
+    k_pkt<NB><<<grid, 256, 0, st>>>(nseg32, kTile, tb);
+    HS_TRY(lc.end());
+  }
   lc.begin("scan_units");
   k_scan_units<<<1, 1024, 0, st>>>(L.npk, tb);
   HS_TRY(lc.end());
@@ -166,10 +185,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
       attr = true;
     }
-    const bool stuck = (o.debug_flags & 1) != 0;
-    const uint64_t limit_ns = stuck ? 2000000ull : 2000000000ull;  // 2 ms when injected, else 2 s
     lc.begin("scatter");
-    kern<<<L.max_blocks, kBlock, smem, st>>>(keys, vals, kw, vw, nseg32, kTile, limit_ns, stuck ? 1 : 0, tb);
+    kern<<<L.max_blocks, kBlock, smem, st>>>(keys, vals, kw, vw, nseg32, kTile, tb);
     HS_TRY(lc.end());
   }
   if (o.stop_after == 1) {
@@ -182,7 +199,10 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       auto kern = k_tilesort<K, HAS_V, kBlock, kIpt>;
       if (!grid) grid = persistent_grid(kern, kBlock, smem);
       lc.begin("tilesort");
-      kern<<<grid, kBlock, smem, st>>>(kw, vw, keys, vals, kw, vw, L.npk, o.stop_after == 2 ? 1 : 0, tb);
+      const bool stuck = (o.debug_flags & 1) != 0;
+      const uint64_t limit_ns = stuck ? 2000000ull : 2000000000ull;  // 2 ms when injected, else 2 s
+      kern<<<grid, kBlock, smem, st>>>(kw, vw, keys, vals, kw, vw, L.npk, o.stop_after == 2 ? 1 : 0, stuck ? 1 : 0,
+                                       limit_ns, tb);
       HS_TRY(lc.end());
     }
     if (o.stop_after == 2) {

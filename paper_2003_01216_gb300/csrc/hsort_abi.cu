@@ -288,8 +288,9 @@ hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, 
   out->part_tile = kTile;
   out->fan_in = 2;
   out->merge_passes = (n == 0) ? 0 : worst_passes(n);
-  // seg_plan, hist (x2 for int32), finalize, scan_units, scatter, tilesort, 2 per merge pass
-  int l = 1 + (dtype == HS_INT32 ? 2 : 1) + 1 + 1 + 1;
+  // seg_plan, hist (x2 for int32), finalize, fold, 3 scan kernels, pkt, scan_units, scatter,
+  // tilesort, 2 per merge pass
+  int l = 1 + (dtype == HS_INT32 ? 2 : 1) + 1 + 1 + 3 + 1 + 1 + 1;
   if (o.stop_after != 1) l += 1;
   if (o.stop_after == 0) l += 2 * out->merge_passes;
   out->launches = (n == 0) ? 0 : l;

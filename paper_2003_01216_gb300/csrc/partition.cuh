@@ -3,30 +3,34 @@
 // digit of its image, keeping input order inside each packet.
 //
 // Kernels, in launch order:
-//   k_seg_plan   segment table and packet-step block prefix (one CTA)
-//   k_hist       per-block class + per-class packet counts (one read of the keys)
-//   k_finalize   per segment: final class, folded packet counts, packet offsets,
-//                tiles per packet
-//   k_scan_units exclusive scan of the tiles per packet (one CTA)
-//   k_scatter    stable scatter into packets with a decoupled look-back across
-//                blocks (one read + one write of keys and values)
+//   k_seg_plan    segment table and packet-step block prefix (one CTA)
+//   k_hist        one read of the keys: per block its class and its packet
+//                 counts under that class; per segment the largest class
+//   k_finalize    per segment: the final class and image
+//   k_fold        per block: its counts under the segment's class, laid out
+//                 in (segment, packet, block) order
+//   k_scan_*      exclusive scan of that array: because the sorted output
+//                 holds segment after segment and, inside one, packet after
+//                 packet in block order, the prefix IS every block's absolute
+//                 first position in every packet
+//   k_pkt         packet offsets and tiles per packet
+//   k_scan_units  exclusive scan of the tiles per packet (one CTA)
+//   k_scatter     stable scatter into packets (one read + one write of the
+//                 keys and values; no block waits on another)
 //
 // The class trick: the packet of a key depends on the class (digit count D,
 // or bit length B) of the LARGEST key image of its array, which no block
 // knows before the whole array has been read.  k_hist therefore counts every
-// block under its own block-local class c_b and files the counts under c_b.
-// A block whose class is below the array's class C holds only keys smaller
-// than every threshold of C (decimal: all its keys fall in packet 0; binary:
-// its local bucket t becomes t >> (shift(C) - shift(c_b))), so k_finalize can
-// fold every row into the counts under C exactly, after one read of the keys.
+// block under its own block-local class c_b.  A block whose class is below
+// the array's class C holds only keys smaller than every threshold of C
+// (decimal: all its keys fall in packet 0; binary: its local bucket t becomes
+// t >> (shift(C) - shift(c_b))), so k_fold turns every block's counts into
+// counts under C exactly, without a second read of the keys.
 #pragma once
 #include "common.cuh"
+#include "scan.cuh"
 
 namespace hs {
-
-constexpr uint64_t kFlagAgg = 1ull << 62;
-constexpr uint64_t kFlagInc = 2ull << 62;
-constexpr uint64_t kValMask = (1ull << 62) - 1;
 
 // ---------------------------------------------------------------------------
 // k_seg_plan: segment table.  Plain sorts pass offs == nullptr (one segment
@@ -107,10 +111,10 @@ __device__ __forceinline__ uint32_t find_seg(const uint32_t* __restrict__ pre, u
 
 // ---------------------------------------------------------------------------
 // k_hist: each CTA walks a contiguous range of packet-step blocks.  For every
-// block it reduces the largest key image, takes the block's class, and counts
-// its keys per packet under that class into a shared-memory table
-// acc[class][packet]; the table is flushed into the segment's global
-// histogram when the segment changes and at the end.
+// block it reduces the largest key image, takes the block's class c_b and
+// counts its keys per packet under c_b; it writes c_b and the NB counts of
+// the block, and keeps the largest class of the current segment, flushed
+// (atomicMax) when the segment changes and at the end.
 //   img = 0: identity image (and every segment's "has a negative key" flag)
 //   img = 1: sign-flipped image, only for segments flagged by the img = 0 pass
 // ---------------------------------------------------------------------------
@@ -118,45 +122,30 @@ template <class K, int NB, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint32_t nseg, uint32_t part_tile,
                                                  int img, Tables tb) {
   using U = typename KT<K>::U;
-  constexpr int NCLS = (NB == 10) ? kDecClasses : kBinClasses;
   constexpr int NW = BLOCK / kWarp;
-  extern __shared__ uint32_t s_acc[];  // [NCLS][NB]
+  __shared__ uint32_t s_cnt[NB];
   __shared__ U s_max[NW];
-  __shared__ uint32_t s_neg;
-  __shared__ unsigned long long s_used[2];
+  __shared__ uint32_t s_neg, s_cmax;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
   const uint32_t total = tb.blk_prefix[nseg];
   const uint32_t per = (total + gridDim.x - 1) / gridDim.x;
   const uint32_t b0 = min(total, blockIdx.x * per), b1 = min(total, b0 + per);
   if (b0 >= b1) return;
-
-  for (int i = tid; i < NCLS * NB; i += BLOCK) s_acc[i] = 0;
   if (tid == 0) {
-    s_used[0] = s_used[1] = 0;
     s_neg = 0;
+    s_cmax = 0;
   }
   __syncthreads();
 
   uint32_t seg = find_seg(tb.blk_prefix, nseg, b0);
-  auto flush = [&](uint32_t s) {
+  auto flush = [&](uint32_t sg) {
     __syncthreads();
-    uint32_t* g = tb.hist + (static_cast<size_t>(s) * 2 + img) * NCLS * NB;
-    for (int c = 0; c < NCLS; ++c) {
-      if (!((s_used[c >> 6] >> (c & 63)) & 1ull)) continue;
-      for (int q = tid; q < NB; q += BLOCK) {
-        uint32_t v = s_acc[c * NB + q];
-        if (v) {
-          atomicAdd(&g[c * NB + q], v);
-          s_acc[c * NB + q] = 0;
-        }
-      }
-    }
-    __syncthreads();  // every thread is done reading s_used before it is cleared
     if (tid == 0) {
-      if (s_neg) atomicOr(&tb.seg_neg[s], 1u);
-      s_used[0] = s_used[1] = 0;
+      if (s_neg) atomicOr(&tb.seg_neg[sg], 1u);
+      if (s_cmax) atomicMax(&tb.seg_cmax[sg * 2 + img], s_cmax);
       s_neg = 0;
+      s_cmax = 0;
     }
     __syncthreads();
   };
@@ -168,19 +157,19 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
     }
     const bool flip = (img == 1);
     if (flip && !tb.seg_neg[seg]) continue;  // block-uniform
-    const uint64_t s_lo = tb.seg_off[seg];
-    const uint64_t beg = s_lo + static_cast<uint64_t>(b - tb.blk_prefix[seg]) * part_tile;
+    const uint64_t beg = tb.seg_off[seg] + static_cast<uint64_t>(b - tb.blk_prefix[seg]) * part_tile;
     const uint32_t cnt = static_cast<uint32_t>(min64(part_tile, tb.seg_off[seg + 1] - beg));
     const K* src = keys + beg;
 
+    for (int q = tid; q < NB; q += BLOCK) s_cnt[q] = 0;
     U u[IPT];
     bool any_neg = false;
     U m = 0;
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-      uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
+      const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
       if (i < cnt) {
-        K k = src[i];
+        const K k = src[i];
         any_neg |= KT<K>::negative(k);
         u[j] = KT<K>::image(k, flip);
         m = max(m, u[j]);
@@ -188,7 +177,6 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
         u[j] = 0;
       }
     }
-    // block max of the images
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, static_cast<U>(__shfl_xor_sync(0xffffffffu, m, o)));
     if (lane == 0) s_max[wid] = m;
@@ -199,110 +187,105 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
     for (int w = 1; w < NW; ++w) m = max(m, s_max[w]);
     const int cls = (NB == 10) ? dec_class(static_cast<uint64_t>(m)) : bin_class(m);
     const DigitRule rule = (NB == 10) ? make_rule_dec(cls) : make_rule_bin(cls);
-    uint32_t* row = s_acc + cls * NB;
 
     if constexpr (NB == 10) {
-      // packed per-thread counters: 6 bits per packet
+      // packed per-thread counters: 6 bits per packet (IPT <= 63)
       unsigned long long pc = 0;
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
-        uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
+        const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
         if (i < cnt) pc += 1ull << (6 * packet_of<NB>(u[j], rule));
       }
 #pragma unroll
       for (int q = 0; q < 10; ++q) {
-        uint32_t c = static_cast<uint32_t>((pc >> (6 * q)) & 63ull);
-        c = __reduce_add_sync(0xffffffffu, c);
-        if (lane == 0 && c) atomicAdd(&row[q], c);
+        const uint32_t c = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>((pc >> (6 * q)) & 63ull));
+        if (lane == 0 && c) atomicAdd(&s_cnt[q], c);
       }
     } else {
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
-        uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
-        uint32_t q = (i < cnt) ? packet_of<NB>(u[j], rule) : NB;
-        uint32_t peers = __match_any_sync(0xffffffffu, q);
-        if (q < NB && lane == __ffs(peers) - 1) atomicAdd(&row[q], __popc(peers));
+        const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
+        const uint32_t q = (i < cnt) ? packet_of<NB>(u[j], rule) : NB;
+        const uint32_t peers = __match_any_sync(0xffffffffu, q);
+        if (q < NB && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[q], __popc(peers));
       }
     }
-    if (tid == 0) atomicOr(&s_used[cls >> 6], 1ull << (cls & 63));
-    __syncthreads();  // s_max reuse
+    __syncthreads();
+    for (int q = tid; q < NB; q += BLOCK) tb.cnt_raw[static_cast<size_t>(b) * NB + q] = s_cnt[q];
+    if (tid == 0) {
+      tb.cls_raw[b] = static_cast<uint32_t>(cls);
+      s_cmax = max(s_cmax, static_cast<uint32_t>(cls));
+    }
+    __syncthreads();  // s_cnt / s_max reuse
   }
   flush(seg);
 }
 
 // ---------------------------------------------------------------------------
-// k_finalize: one warp per segment (kFinWarps segments per CTA).  Picks the
-// image (flipped when the segment holds a negative int32 key), the segment
-// class C = largest class with a non-empty row, folds every row into the
-// packet counts under C, and writes packet offsets and tiles per packet.
+// k_finalize: one thread per segment: the image (flipped when the segment
+// holds a negative int32 key) and the segment class C.
 // ---------------------------------------------------------------------------
-constexpr int kFinWarps = 8;
-
 template <int NB>
-__global__ void __launch_bounds__(kFinWarps * 32) k_finalize(uint32_t nseg, uint32_t tile, Tables tb) {
-  constexpr int NCLS = (NB == 10) ? kDecClasses : kBinClasses;
-  __shared__ uint32_t s_cnt[kFinWarps][NB];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const uint32_t s = blockIdx.x * kFinWarps + wib;
+__global__ void k_finalize(uint32_t nseg, Tables tb) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
-  uint32_t* cnt = s_cnt[wib];
-  for (int q = lane; q < NB; q += 32) cnt[q] = 0;
-  __syncwarp();
   const uint32_t neg = tb.seg_neg[s];
-  const uint32_t* h = tb.hist + (static_cast<size_t>(s) * 2 + (neg ? 1 : 0)) * NCLS * NB;
-  // largest class with a non-empty row
-  int C = -1;
-  for (int c = NCLS - 1; c >= 0 && C < 0; --c) {
-    bool nz = false;
-    for (int q = lane; q < NB; q += 32) nz |= h[c * NB + q] != 0;
-    if (__any_sync(0xffffffffu, nz)) C = c;
-  }
-  if (C >= 0) {
+  const bool empty = tb.blk_prefix[s + 1] == tb.blk_prefix[s];
+  const uint32_t C = tb.seg_cmax[s * 2 + (neg ? 1 : 0)];
+  tb.seg_class[s] = empty ? (NB == 10 ? 1u : 0u) : C;
+  tb.seg_flip[s] = neg;
+}
+
+// ---------------------------------------------------------------------------
+// k_fold: block b's count for packet p under its segment's class C, written
+// at (segment s, packet p, block b): index blk_prefix[s]*NB + p*nb_s + (b - first block).
+// ---------------------------------------------------------------------------
+template <int NB>
+__global__ void k_fold(uint32_t nseg, Tables tb) {
+  const uint32_t total = tb.blk_prefix[nseg];
+  const uint64_t m = static_cast<uint64_t>(total) * NB;
+  for (uint64_t idx = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; idx < m;
+       idx += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const uint32_t b = static_cast<uint32_t>(idx / NB), p = static_cast<uint32_t>(idx % NB);
+    const uint32_t s = find_seg(tb.blk_prefix, nseg, b);
+    const uint32_t first = tb.blk_prefix[s], nb_s = tb.blk_prefix[s + 1] - first;
+    const uint32_t C = tb.seg_class[s], cb = tb.cls_raw[b];
+    const uint32_t* raw = tb.cnt_raw + static_cast<size_t>(b) * NB;
+    uint32_t v = 0;
     if constexpr (NB == 10) {
-      // every key of a row below C falls in packet 0
-      uint32_t low = 0;
-      for (int c = 0; c < C; ++c)
-        if (lane < NB) low += h[c * NB + lane];
-      low = __reduce_add_sync(0xffffffffu, low);
-      if (lane < NB) cnt[lane] = h[C * NB + lane] + (lane == 0 ? low : 0);
-    } else {
-      // a row of class c holds buckets under shift(c); under shift(C) its
-      // bucket t becomes t >> (shift(C) - shift(c))
-      const int shC = C > 8 ? C - 8 : 0;
-      for (int c = 0; c <= C; ++c) {
-        const int d = shC - (c > 8 ? c - 8 : 0);
-        for (int t = lane; t < NB; t += 32) {
-          const uint32_t v = h[c * NB + t];
-          if (v) atomicAdd(&cnt[t >> d], v);
-        }
-      }
-    }
-  }
-  __syncwarp();
-  uint64_t* po = tb.pkt_off + static_cast<size_t>(s) * NB;
-  uint32_t* up = tb.unit_prefix + static_cast<size_t>(s) * NB;
-  // exclusive prefix over packets, 32 at a time, in packet order
-  uint64_t run = tb.seg_off[s];
-  for (int q0 = 0; q0 < NB; q0 += 32) {
-    const int q = q0 + lane;
-    const uint32_t c = (q < NB) ? cnt[q] : 0;
-    uint32_t v = c;
+      if (cb == C) {
+        v = raw[p];
+      } else if (p == 0) {  // every key of the block is below 10^(C-1): packet 0
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t x = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += x;
+        for (int t = 0; t < 10; ++t) v += raw[t];
+      }
+    } else {
+      const uint32_t d = (C > 8 ? C - 8 : 0) - (cb > 8 ? cb - 8 : 0);
+      const uint32_t lo = p << d, hi = min(static_cast<uint32_t>(NB), (p + 1) << d);
+      for (uint32_t t = lo; t < hi; ++t) v += raw[t];
     }
-    if (q < NB) {
-      po[q] = run + (v - c);
-      up[q] = (c + tile - 1) / tile;
-    }
-    run += __shfl_sync(0xffffffffu, v, 31);
+    tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s + (b - first)] = v;
   }
-  if (lane == 0) {
-    tb.seg_class[s] = C >= 0 ? static_cast<uint32_t>(C) : (NB == 10 ? 1u : 0u);
-    tb.seg_flip[s] = neg;
-    if (s == nseg - 1) tb.pkt_off[static_cast<size_t>(nseg) * NB] = tb.seg_off[nseg];
+}
+
+// ---------------------------------------------------------------------------
+// k_pkt: per (segment, packet): the packet's absolute start and its tiles.
+// ---------------------------------------------------------------------------
+template <int NB>
+__global__ void k_pkt(uint32_t nseg, uint32_t tile, Tables tb) {
+  const uint64_t m = static_cast<uint64_t>(nseg) * NB;
+  for (uint64_t idx = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; idx < m;
+       idx += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const uint32_t s = static_cast<uint32_t>(idx / NB), p = static_cast<uint32_t>(idx % NB);
+    const uint32_t first = tb.blk_prefix[s], nb_s = tb.blk_prefix[s + 1] - first;
+    const uint64_t start = nb_s ? tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s]
+                                : tb.seg_off[s];
+    const uint64_t end = (nb_s && p + 1 < NB) ? tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p + 1) * nb_s]
+                                                : tb.seg_off[s + 1];
+    tb.pkt_off[idx] = start;
+    tb.unit_prefix[idx] = static_cast<uint32_t>((end - start + tile - 1) / tile);
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) tb.pkt_off[m] = tb.seg_off[nseg];
 }
 
 // ---------------------------------------------------------------------------
@@ -346,165 +329,112 @@ static __global__ void k_scan_units(uint32_t m, Tables tb) {
 }
 
 // ---------------------------------------------------------------------------
-// k_scatter: stable move into packets.  Blocks take tickets in launch order
-// so every block's predecessor is resident or finished (no deadlock).  Inside
-// a block, each warp ranks its keys in input order (warp-striped items, a
-// match over packet ids); warps are ordered by position; across blocks of the
-// same segment a decoupled look-back over per-(block, packet) status words
-// gives each packet's count in earlier blocks.  Keys are staged in shared
-// memory grouped by packet and written out as contiguous runs.
-//
-// Bounded wait: a status word not published within `limit_ns` (globaltimer)
-// sets kErrTimeout; the block then publishes a value anyway so its successors
-// do not wait, and writes nothing.  Every write is checked against its packet's
-// bounds (kErrBounds on violation, write skipped).
+// k_scatter: stable move into packets, one CTA per packet-step block.  Each
+// warp ranks its keys in input order (warp-striped items, a match over packet
+// ids); warps are ordered by position; the block's absolute first position
+// in every packet comes from the scan.  Keys are staged in shared memory
+// grouped by packet and written out as contiguous runs.  Every write is
+// checked against its packet's end (kErrBounds on violation, write skipped).
 // ---------------------------------------------------------------------------
 template <class K, bool HAS_V, int NB, int BLOCK, int IPT>
-__global__ void __launch_bounds__(BLOCK) k_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+__global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                                                     K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                                                    uint32_t nseg, uint32_t part_tile, uint64_t limit_ns,
-                                                    int debug_stuck, Tables tb) {
-  using U = typename KT<K>::U;
+                                                    uint32_t nseg, uint32_t part_tile, Tables tb) {
   constexpr int NW = BLOCK / kWarp;
   constexpr int TILE = BLOCK * IPT;
   constexpr int NBX = NB + 1;  // + a dummy packet for lanes past the end
   extern __shared__ __align__(128) unsigned char s_raw[];
-  K* s_keys = reinterpret_cast<K*>(s_raw);                                    // TILE
-  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + TILE);             // TILE (pairs)
-  uint32_t* s_wc = s_vals + (HAS_V ? TILE : 0);                              // NW * NBX warp counts
-  uint32_t* s_tot = s_wc + NW * NBX;                                         // NB block totals
-  uint32_t* s_bs = s_tot + ((NB + 1) & ~1);                                  // NB + 1 block packet starts
-  unsigned long long* s_gb = reinterpret_cast<unsigned long long*>(s_bs + ((NB + 2) & ~1));  // NB
-  uint16_t* s_pk = reinterpret_cast<uint16_t*>(s_gb + NB);                   // TILE packet ids
-  __shared__ uint32_t s_ticket, s_fail;
+  K* s_keys = reinterpret_cast<K*>(s_raw);                               // TILE
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + TILE);        // TILE (pairs)
+  uint32_t* s_wc = s_vals + (HAS_V ? TILE : 0);                         // NW * NBX warp counts
+  uint32_t* s_bs = s_wc + NW * NBX;                                     // NB + 1 block packet starts
+  uint32_t* s_gb = s_bs + ((NB + 2) & ~1);                              // NB absolute bases
+  uint16_t* s_pk = reinterpret_cast<uint16_t*>(s_gb + ((NB + 1) & ~1)); // TILE packet ids
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) {
-    s_ticket = atomicAdd(&tb.counters[0], 1u);
-    s_fail = 0;
-  }
-  for (int i = tid; i < NW * NBX; i += BLOCK) s_wc[i] = 0;
-  __syncthreads();
-  const uint32_t t = s_ticket;
+  const uint32_t b = blockIdx.x;
   const uint32_t total = tb.blk_prefix[nseg];
-  if (t >= total) return;
-  const uint32_t seg = find_seg(tb.blk_prefix, nseg, t);
-  const uint32_t first = tb.blk_prefix[seg];
-  const uint64_t beg = tb.seg_off[seg] + static_cast<uint64_t>(t - first) * part_tile;
+  if (b >= total) return;
+  for (int i = tid; i < NW * NBX; i += BLOCK) s_wc[i] = 0;
+  const uint32_t seg = find_seg(tb.blk_prefix, nseg, b);
+  const uint32_t first = tb.blk_prefix[seg], nb_s = tb.blk_prefix[seg + 1] - first;
+  const uint64_t beg = tb.seg_off[seg] + static_cast<uint64_t>(b - first) * part_tile;
   const uint32_t cnt = static_cast<uint32_t>(min64(part_tile, tb.seg_off[seg + 1] - beg));
   const bool flip = tb.seg_flip[seg] != 0;
   const int cls = static_cast<int>(tb.seg_class[seg]);
   const DigitRule rule = (NB == 10) ? make_rule_dec(cls) : make_rule_bin(cls);
+  // absolute first position of this block's keys in every packet
+  for (int p = tid; p < NB; p += BLOCK)
+    s_gb[p] = tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s + (b - first)];
+  __syncthreads();
 
-  // load (warp-striped) and compute packets
+  // load (warp-striped) and compute packets; rank and packet share a register
   K k[IPT];
   uint32_t v[IPT];
-  uint32_t q[IPT];
+  uint32_t rq[IPT];  // packet in bits 0..15, warp rank in bits 16..31
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
     const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
     if (i < cnt) {
       k[j] = keys_in[beg + i];
       if constexpr (HAS_V) v[j] = vals_in[beg + i];
-      q[j] = packet_of<NB>(KT<K>::image(k[j], flip), rule);
+      rq[j] = packet_of<NB>(KT<K>::image(k[j], flip), rule);
     } else {
-      q[j] = NB;
+      rq[j] = NB;
     }
   }
   // warp ranking in input order
-  uint32_t r[IPT];
   uint32_t* wc = s_wc + wid * NBX;
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
-    const uint32_t peers = __match_any_sync(0xffffffffu, q[j]);
-    const uint32_t base = wc[q[j]];
-    r[j] = base + __popc(peers & lt_mask);
+    const uint32_t q = rq[j];
+    const uint32_t peers = __match_any_sync(0xffffffffu, q);
+    const uint32_t base = wc[q];
+    rq[j] = q | ((base + __popc(peers & lt_mask)) << 16);
     __syncwarp();
-    if (lane == __ffs(peers) - 1) wc[q[j]] = base + __popc(peers);
+    if (lane == __ffs(peers) - 1) wc[q] = base + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  // per packet: block total, warp prefixes (in place in s_wc), block starts
+  // per packet: warp prefixes (in place in s_wc) and block totals
   for (int p = tid; p < NB; p += BLOCK) {
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
-      uint32_t c = s_wc[w * NBX + p];
+      const uint32_t c = s_wc[w * NBX + p];
       s_wc[w * NBX + p] = run;
       run += c;
     }
-    s_tot[p] = run;
+    s_bs[p] = run;
   }
   __syncthreads();
-  // look-back (thread p for packet p) + exclusive scan of block totals
-  if (tid < NB) {
-    const int p = tid;
-    const uint32_t agg = s_tot[p];
-    uint64_t* st = tb.status + static_cast<size_t>(t) * NB;
-    const bool stuck = debug_stuck && (t == tb.blk_prefix[0] + 1);
-    uint64_t excl = 0;
-    if (t == first) {
-      st_relaxed(&st[p], kFlagInc | agg);
-    } else {
-      if (!stuck) st_relaxed(&st[p], kFlagAgg | agg);
-      int64_t pred = static_cast<int64_t>(t) - 1;
-      uint64_t t0 = 0;
-      uint64_t spins = 0;
-      while (true) {
-        const uint64_t w = ld_relaxed(tb.status + static_cast<size_t>(pred) * NB + p);
-        const uint64_t f = w & ~kValMask;
-        if (f == 0) {
-          // two bounds: elapsed globaltimer time, and (should the timer not
-          // advance) an iteration count of at least that many nanoseconds
-          ++spins;
-          if ((spins & 63) == 0) {
-            const uint64_t now = globaltimer_ns();
-            if (t0 == 0) t0 = now;
-            if (now - t0 > limit_ns || spins > (limit_ns >> 4)) {
-              s_fail = 1;
-              break;
-            }
-          }
-          __nanosleep(32);
-          continue;
-        }
-        excl += w & kValMask;
-        if (f == kFlagInc) break;
-        --pred;
-      }
-      if (!stuck) st_relaxed(&st[p], kFlagInc | (excl + agg));
-    }
-    s_gb[p] = tb.pkt_off[static_cast<size_t>(seg) * NB + p] + excl;
-  }
-  if (tid == 0) {  // block packet starts: exclusive scan of the totals (s_tot stays intact)
+  if (tid == 0) {  // block packet starts: exclusive scan of the totals
     uint32_t run = 0;
     for (int p = 0; p < NB; ++p) {
+      const uint32_t c = s_bs[p];
       s_bs[p] = run;
-      run += s_tot[p];
+      run += c;
     }
     s_bs[NB] = run;
   }
   __syncthreads();
-  if (s_fail) {
-    if (tid == 0) atomicOr(tb.err, kErrTimeout);
-    return;
-  }
   // stage grouped by packet, in input order inside each packet
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
-    if (q[j] < NB) {
-      const uint32_t pos = s_bs[q[j]] + s_wc[wid * NBX + q[j]] + r[j];
+    const uint32_t q = rq[j] & 0xffffu;
+    if (q < NB) {
+      const uint32_t pos = s_bs[q] + s_wc[wid * NBX + q] + (rq[j] >> 16);
       s_keys[pos] = k[j];
       if constexpr (HAS_V) s_vals[pos] = v[j];
-      s_pk[pos] = static_cast<uint16_t>(q[j]);
+      s_pk[pos] = static_cast<uint16_t>(q);
     }
   }
   __syncthreads();
   const uint64_t* pend = tb.pkt_off + static_cast<size_t>(seg) * NB + 1;
   for (uint32_t e = tid; e < cnt; e += BLOCK) {
     const uint32_t p = s_pk[e];
-    const uint64_t dst = s_gb[p] + (e - s_bs[p]);
+    const uint64_t dst = static_cast<uint64_t>(s_gb[p]) + (e - s_bs[p]);
     if (dst >= pend[p]) {
       atomicOr(tb.err, kErrBounds);
       continue;

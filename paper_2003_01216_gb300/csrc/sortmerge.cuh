@@ -256,7 +256,7 @@ constexpr uint64_t kWaitNs = 2000000000ull;  // bounded waits on copies: 2 s
 template <class K, bool HAS_V, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, const uint32_t* __restrict__ vw, K* ku,
                                                      uint32_t* vu, K* kw_out, uint32_t* vw_out, uint32_t npk,
-                                                     int force_w, Tables tb) {
+                                                     int force_w, int debug_stuck, uint64_t limit_ns, Tables tb) {
   constexpr int TILE = BLOCK * IPT;
   constexpr int RE = region_elems(TILE);
   extern __shared__ __align__(128) unsigned char s_raw[];
@@ -295,12 +295,15 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
       cp_async_mbar_arrive(&s_bar);
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive_expect_tx(&s_bar, bk.bytes + bv.bytes);
+        // testing hook: CTA 0 announces 16 bytes that never arrive on its
+        // first tile, so its bounded wait expires
+        const uint32_t extra = (debug_stuck && blockIdx.x == 0 && u == blockIdx.x) ? 16u : 0u;
+        mbar_arrive_expect_tx(&s_bar, bk.bytes + bv.bytes + extra);
         if (bk.bytes) bulk_g2s(bk.sdst, bk.gsrc, bk.bytes, &s_bar);
         if (HAS_V && bv.bytes) bulk_g2s(bv.sdst, bv.gsrc, bv.bytes, &s_bar);
       }
     }
-    const bool ok = mbar_wait_bounded(&s_bar, parity, tb.err, kWaitNs);
+    const bool ok = mbar_wait_bounded(&s_bar, parity, tb.err, limit_ns);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
@@ -365,7 +368,7 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
   }
   // a copy may still be in flight into the region: give it a bounded chance
   // to land before the CTA's shared memory is released
-  if (failed) mbar_wait_bounded(&s_bar, parity, tb.err, kWaitNs);
+  if (failed) mbar_wait_bounded(&s_bar, parity, tb.err, limit_ns);
   if (tid == 0) bulk_wait0();
 }
 

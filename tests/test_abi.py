@@ -76,9 +76,10 @@ def test_plan_describe(n):
     tiles = -(-n // tile)
     passes = 0 if tiles <= 1 else math.ceil(math.log2(tiles))
     assert p["merge_passes"] == passes
-    # seg_plan, 2 histogram passes (int32), finalize, scan, scatter, tile sort, 2 per merge pass
-    assert p["launches"] == 7 + 2 * passes
-    assert hs.plan(N.HS_UINT64, n)["launches"] == 6 + 2 * passes
+    # seg_plan, 2 histogram passes (int32), finalize, fold, 3 scan kernels, packet offsets,
+    # tile prefix, scatter, tile sort, 2 per merge pass
+    assert p["launches"] == 12 + 2 * passes
+    assert hs.plan(N.HS_UINT64, n)["launches"] == 11 + 2 * passes
 
 
 def test_workspace_size_grows_with_n():
