@@ -64,14 +64,29 @@ __host__ __device__ __forceinline__ uint64_t pow10_u64(int e) {
 }
 
 // Decimal digit count of v: 1 + number of powers 10^k (k >= 1) not above v.
+struct Pow10Table {
+  uint64_t p[20];
+};
+__host__ __device__ constexpr Pow10Table make_pow10() {
+  Pow10Table t{};
+  uint64_t v = 1;
+  for (int k = 0; k < 20; ++k) {
+    t.p[k] = v;
+    v *= 10ull;
+  }
+  return t;
+}
+static __constant__ Pow10Table c_pow10 = make_pow10();
+__device__ __forceinline__ int dec_class(uint32_t v) {  // 32-bit images: at most 10 digits
+  int d = 1;
+#pragma unroll
+  for (int k = 1; k <= 9; ++k) d += (v >= c_pow10.p[k]) ? 1 : 0;
+  return d;
+}
 __device__ __forceinline__ int dec_class(uint64_t v) {
   int d = 1;
-  uint64_t p = 10;
 #pragma unroll
-  for (int k = 1; k <= 19; ++k) {
-    d += (v >= p) ? 1 : 0;
-    p *= 10ull;
-  }
+  for (int k = 1; k <= 19; ++k) d += (v >= c_pow10.p[k]) ? 1 : 0;
   return d;
 }
 __device__ __forceinline__ int bin_class(uint32_t v) { return 32 - __clz(v); }
@@ -84,19 +99,30 @@ struct DigitRule {
   uint32_t shift;    // 256-bucket: max(0, B - 8)
 };
 
-__device__ __forceinline__ DigitRule make_rule_dec(int D) {
+__host__ __device__ constexpr DigitRule rule_dec_c(int D) {
   DigitRule r{};
-  uint64_t div = pow10_u64(D - 1);
+  uint64_t div = 1;
+  for (int i = 1; i < D; ++i) div *= 10ull;
   r.mult = (div == 1) ? 0ull : (~0ull / div) + 1ull;
-#pragma unroll
-  for (int j = 1; j <= 9; ++j) {
-    // j * div - 1 without overflow; saturate when j * div > 2^64 - 1
-    uint64_t lim = ~0ull / div;  // largest j with j * div representable
+  const uint64_t lim = ~0ull / div;  // largest j with j * div representable
+  for (int j = 1; j <= 9; ++j)
     r.thr[j - 1] = (static_cast<uint64_t>(j) <= lim) ? static_cast<uint64_t>(j) * div - 1ull : ~0ull;
-  }
   r.shift = 0;
   return r;
 }
+struct DecRuleTable {
+  DigitRule r[kDecClasses];
+};
+__host__ __device__ constexpr DecRuleTable make_dec_rules() {
+  DecRuleTable t{};
+  for (int D = 1; D < kDecClasses; ++D) t.r[D] = rule_dec_c(D);
+  return t;
+}
+// The decimal rules of every digit width, built at compile time (the 64-bit
+// divisions they need never run on the device).
+static __constant__ DecRuleTable c_dec_rules = make_dec_rules();
+
+__device__ __forceinline__ const DigitRule& rule_dec(int D) { return c_dec_rules.r[D]; }
 __device__ __forceinline__ DigitRule make_rule_bin(int B) {
   DigitRule r{};
   r.shift = B > 8 ? static_cast<uint32_t>(B - 8) : 0u;
@@ -157,6 +183,7 @@ struct Tables {
                           // order, then scanned in place into absolute first positions
   uint32_t* scan_part;    // scan partials
   uint32_t* seg_neg;      // nseg: segment holds a negative int32 key
+  uint32_t* any_neg;      // 1 word: some segment holds a negative int32 key
   uint32_t* seg_cmax;     // nseg * 2: largest block class (identity image, flipped image)
   uint32_t* seg_class;    // nseg: final class (D or B) of the segment
   uint32_t* seg_flip;     // nseg: sign flip in use

@@ -5,7 +5,7 @@
 #include <cstdio>
 #include <cstring>
 
-#include "../../include/hsort.h"
+#include "hsort.h"
 #include "common.cuh"
 #include "partition.cuh"
 #include "sortmerge.cuh"
@@ -22,7 +22,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
   size_t keys_w, vals_w, seg_off, blk_prefix, cls_raw, cnt_raw, flat, scan_part, seg_neg, seg_cmax, seg_class,
-      seg_flip, pkt_off, unit_prefix, recs, total;
+      seg_flip, pkt_off, unit_prefix, recs, any_neg, total;
   uint32_t max_blocks, max_units, npk;
 };
 
@@ -52,6 +52,7 @@ inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg
   L.pkt_off = take((L.npk + 1) * 8);
   L.unit_prefix = take((L.npk + 1) * 4);
   L.recs = take((static_cast<size_t>(L.max_units) + 1) * sizeof(MergeRec));
+  L.any_neg = take(4);
   L.total = off;
   return L;
 }
@@ -70,6 +71,7 @@ inline Tables make_tables(char* base, const Layout& L, uint32_t* err) {
   t.seg_flip = reinterpret_cast<uint32_t*>(base + L.seg_flip);
   t.pkt_off = reinterpret_cast<uint64_t*>(base + L.pkt_off);
   t.unit_prefix = reinterpret_cast<uint32_t*>(base + L.unit_prefix);
+  t.any_neg = reinterpret_cast<uint32_t*>(base + L.any_neg);
   t.err = err;
   return t;
 }
@@ -94,13 +96,17 @@ inline size_t scatter_smem() {
   b += kTile * 2;
   return b;
 }
+template <class K>
+inline size_t hist_smem() {  // two stages of keys
+  return 2 * ((region_elems(kTile) * sizeof(K) + 127) & ~size_t(127));
+}
 template <class K, bool HAS_V>
 inline size_t sort_smem() {  // one region of keys (and values)
   return merge_stage_bytes<K, HAS_V>(kTile);
 }
 template <class K, bool HAS_V>
-inline size_t merge_smem() {  // two pipeline stages
-  return 2 * merge_stage_bytes<K, HAS_V>(kTile);
+inline size_t merge_smem() {  // two input stages (+ two output buffers for 4-byte keys)
+  return merge_buffers<K, HAS_V>() * merge_stage_bytes<K, HAS_V>(kTile);
 }
 
 template <class Kern>
@@ -130,6 +136,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
   // zero the per-segment flags and maxima
   HS_TRY(lc.memset("zero_seg", tb.seg_neg, 0, nseg * 4));
   HS_TRY(lc.memset("zero_cmax", tb.seg_cmax, 0, nseg * 2 * 4));
+  HS_TRY(lc.memset("zero_anyneg", tb.any_neg, 0, 4));
 
   lc.begin("seg_plan");
   k_seg_plan<<<1, 1024, 0, st>>>(offs, nseg32, n, kTile, tb);
@@ -137,11 +144,12 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
 
   {
     static int grid = 0;
+    const size_t smem = hist_smem<K>();
     auto kern = k_hist<K, NB, kBlock, kIpt>;
-    if (!grid) grid = persistent_grid(kern, kBlock, 0);
+    if (!grid) grid = persistent_grid(kern, kBlock, smem);
     for (int img = 0; img < (std::is_same<K, int32_t>::value ? 2 : 1); ++img) {
       lc.begin(img ? "hist_flip" : "hist");
-      kern<<<grid, kBlock, 0, st>>>(keys, nseg32, kTile, img, tb);
+      kern<<<grid, kBlock, smem, st>>>(keys, nseg32, kTile, img, tb);
       HS_TRY(lc.end());
     }
   }

@@ -27,8 +27,10 @@
 // t >> (shift(C) - shift(c_b))), so k_fold turns every block's counts into
 // counts under C exactly, without a second read of the keys.
 #pragma once
+#include "async.cuh"
 #include "common.cuh"
 #include "scan.cuh"
+#include "sortmerge.cuh"
 
 namespace hs {
 
@@ -115,19 +117,87 @@ __device__ __forceinline__ uint32_t find_seg(const uint32_t* __restrict__ pre, u
 // counts its keys per packet under c_b; it writes c_b and the NB counts of
 // the block, and keeps the largest class of the current segment, flushed
 // (atomicMax) when the segment changes and at the end.
-//   img = 0: identity image (and every segment's "has a negative key" flag)
-//   img = 1: sign-flipped image, only for segments flagged by the img = 0 pass
+//   img = 0: identity image (and every segment's "has a negative key" flag);
+//            the keys of block b+1 arrive by bulk copy into the other of two
+//            shared-memory stages while block b is counted
+//   img = 1: sign-flipped image, only for blocks of segments flagged by the
+//            img = 0 pass (plain loads; the kernel returns at once when no
+//            segment holds a negative key)
 // ---------------------------------------------------------------------------
+template <class K, int NB, int BLOCK, int IPT>
+__device__ __forceinline__ void hist_count_block(const K* keysrc, bool from_smem, uint32_t cnt, bool flip, int img,
+                                                 uint32_t* s_cnt, typename KT<K>::U* s_max, uint32_t& s_neg,
+                                                 int& cls_out) {
+  using U = typename KT<K>::U;
+  constexpr int NW = BLOCK / kWarp;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int q = tid; q < NB; q += BLOCK) s_cnt[q] = 0;
+  U u[IPT];
+  bool any_neg = false;
+  U m = 0;
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
+    if (i < cnt) {
+      const K k = keysrc[i];
+      any_neg |= KT<K>::negative(k);
+      u[j] = KT<K>::image(k, flip);
+      m = max(m, u[j]);
+    } else {
+      u[j] = 0;
+    }
+  }
+  (void)from_smem;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, static_cast<U>(__shfl_xor_sync(0xffffffffu, m, o)));
+  if (lane == 0) s_max[wid] = m;
+  if (img == 0 && __any_sync(0xffffffffu, any_neg) && lane == 0) s_neg = 1;
+  __syncthreads();
+  m = s_max[0];
+#pragma unroll
+  for (int w = 1; w < NW; ++w) m = max(m, s_max[w]);
+  const int cls = (NB == 10) ? dec_class(m) : bin_class(m);
+  const DigitRule rule = (NB == 10) ? rule_dec(cls) : make_rule_bin(cls);
+  if constexpr (NB == 10) {
+    // packed per-thread counters: 6 bits per packet (IPT <= 63)
+    unsigned long long pc = 0;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
+      if (i < cnt) pc += 1ull << (6 * packet_of<NB>(u[j], rule));
+    }
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      const uint32_t c = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>((pc >> (6 * q)) & 63ull));
+      if (lane == 0 && c) atomicAdd(&s_cnt[q], c);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
+      const uint32_t q = (i < cnt) ? packet_of<NB>(u[j], rule) : NB;
+      const uint32_t peers = __match_any_sync(0xffffffffu, q);
+      if (q < NB && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[q], __popc(peers));
+    }
+  }
+  cls_out = cls;
+  __syncthreads();
+}
+
 template <class K, int NB, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint32_t nseg, uint32_t part_tile,
                                                  int img, Tables tb) {
   using U = typename KT<K>::U;
   constexpr int NW = BLOCK / kWarp;
+  constexpr int TILE = BLOCK * IPT;
+  extern __shared__ __align__(128) unsigned char s_raw[];  // img 0: two stages of (TILE + 8) keys
   __shared__ uint32_t s_cnt[NB];
   __shared__ U s_max[NW];
   __shared__ uint32_t s_neg, s_cmax;
+  __shared__ __align__(8) uint64_t s_bar[2];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
+  if (img == 1 && *tb.any_neg == 0) return;
   const uint32_t total = tb.blk_prefix[nseg];
   const uint32_t per = (total + gridDim.x - 1) / gridDim.x;
   const uint32_t b0 = min(total, blockIdx.x * per), b1 = min(total, b0 + per);
@@ -135,88 +205,82 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
   if (tid == 0) {
     s_neg = 0;
     s_cmax = 0;
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
   }
+  mbar_fence_init();
   __syncthreads();
 
   uint32_t seg = find_seg(tb.blk_prefix, nseg, b0);
   auto flush = [&](uint32_t sg) {
     __syncthreads();
     if (tid == 0) {
-      if (s_neg) atomicOr(&tb.seg_neg[sg], 1u);
+      if (s_neg) {
+        atomicOr(&tb.seg_neg[sg], 1u);
+        atomicOr(tb.any_neg, 1u);
+      }
       if (s_cmax) atomicMax(&tb.seg_cmax[sg * 2 + img], s_cmax);
       s_neg = 0;
       s_cmax = 0;
     }
     __syncthreads();
   };
+  // where block bb's keys live (segment found by advancing from `sg`)
+  auto block_span = [&](uint32_t bb, uint32_t sg, uint64_t& beg, uint32_t& cnt) {
+    while (bb >= tb.blk_prefix[sg + 1]) ++sg;
+    beg = tb.seg_off[sg] + static_cast<uint64_t>(bb - tb.blk_prefix[sg]) * part_tile;
+    cnt = static_cast<uint32_t>(min64(part_tile, tb.seg_off[sg + 1] - beg));
+  };
+  constexpr size_t STAGE = ((region_elems(TILE) * sizeof(K) + 127) & ~size_t(127));
+  auto issue = [&](uint32_t bb, int st) {  // warp 0
+    uint64_t beg;
+    uint32_t cnt;
+    block_span(bb, seg, beg, cnt);
+    if (lane == 0) fence_proxy_async();  // generic reads of this stage happened before the last barrier
+    __syncwarp();
+    K* region = reinterpret_cast<K*>(s_raw + st * STAGE);
+    const PendingBulk<K> pk = load_window_singles(region, phase_of(keys + beg), keys + beg, cnt, lane);
+    cp_async_mbar_arrive(&s_bar[st]);
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&s_bar[st], pk.bytes);
+      if (pk.bytes) bulk_g2s(pk.sdst, pk.gsrc, pk.bytes, &s_bar[st]);
+    }
+  };
 
+  if (img == 0 && wid == 0) issue(b0, 0);
+  uint32_t par0 = 0, par1 = 0;
+  int st = 0;
   for (uint32_t b = b0; b < b1; ++b) {
     while (b >= tb.blk_prefix[seg + 1]) {
       flush(seg);
       ++seg;
     }
-    const bool flip = (img == 1);
-    if (flip && !tb.seg_neg[seg]) continue;  // block-uniform
     const uint64_t beg = tb.seg_off[seg] + static_cast<uint64_t>(b - tb.blk_prefix[seg]) * part_tile;
     const uint32_t cnt = static_cast<uint32_t>(min64(part_tile, tb.seg_off[seg + 1] - beg));
-    const K* src = keys + beg;
-
-    for (int q = tid; q < NB; q += BLOCK) s_cnt[q] = 0;
-    U u[IPT];
-    bool any_neg = false;
-    U m = 0;
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
-      if (i < cnt) {
-        const K k = src[i];
-        any_neg |= KT<K>::negative(k);
-        u[j] = KT<K>::image(k, flip);
-        m = max(m, u[j]);
-      } else {
-        u[j] = 0;
+    int cls = 0;
+    if (img == 0) {
+      if (wid == 0 && b + 1 < b1) issue(b + 1, st ^ 1);
+      const bool ok = mbar_wait_bounded(&s_bar[st], st ? par1 : par0, tb.err, 2000000000ull);
+      if (st) par1 ^= 1; else par0 ^= 1;
+      if (__syncthreads_or(!ok)) {
+        // the other stage may still be loading: bounded wait, then leave
+        mbar_wait_bounded(&s_bar[st ^ 1], st ? par0 : par1, tb.err, 2000000000ull);
+        return;
       }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, static_cast<U>(__shfl_xor_sync(0xffffffffu, m, o)));
-    if (lane == 0) s_max[wid] = m;
-    if (img == 0 && __any_sync(0xffffffffu, any_neg) && lane == 0) s_neg = 1;
-    __syncthreads();
-    m = s_max[0];
-#pragma unroll
-    for (int w = 1; w < NW; ++w) m = max(m, s_max[w]);
-    const int cls = (NB == 10) ? dec_class(static_cast<uint64_t>(m)) : bin_class(m);
-    const DigitRule rule = (NB == 10) ? make_rule_dec(cls) : make_rule_bin(cls);
-
-    if constexpr (NB == 10) {
-      // packed per-thread counters: 6 bits per packet (IPT <= 63)
-      unsigned long long pc = 0;
-#pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
-        if (i < cnt) pc += 1ull << (6 * packet_of<NB>(u[j], rule));
-      }
-#pragma unroll
-      for (int q = 0; q < 10; ++q) {
-        const uint32_t c = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>((pc >> (6 * q)) & 63ull));
-        if (lane == 0 && c) atomicAdd(&s_cnt[q], c);
-      }
+      const K* region = reinterpret_cast<const K*>(s_raw + st * STAGE) + phase_of(keys + beg);
+      hist_count_block<K, NB, BLOCK, IPT>(region, true, cnt, false, 0, s_cnt, s_max, s_neg, cls);
+      st ^= 1;
     } else {
-#pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
-        const uint32_t q = (i < cnt) ? packet_of<NB>(u[j], rule) : NB;
-        const uint32_t peers = __match_any_sync(0xffffffffu, q);
-        if (q < NB && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[q], __popc(peers));
-      }
+      if (!tb.seg_neg[seg]) continue;  // block-uniform
+      hist_count_block<K, NB, BLOCK, IPT>(keys + beg, false, cnt, true, 1, s_cnt, s_max, s_neg, cls);
     }
-    __syncthreads();
     for (int q = tid; q < NB; q += BLOCK) tb.cnt_raw[static_cast<size_t>(b) * NB + q] = s_cnt[q];
     if (tid == 0) {
       tb.cls_raw[b] = static_cast<uint32_t>(cls);
       s_cmax = max(s_cmax, static_cast<uint32_t>(cls));
     }
-    __syncthreads();  // s_cnt / s_max reuse
+    __syncthreads();  // s_cnt reuse; the stage just read may be refilled
   }
   flush(seg);
 }
@@ -362,7 +426,7 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
   const uint32_t cnt = static_cast<uint32_t>(min64(part_tile, tb.seg_off[seg + 1] - beg));
   const bool flip = tb.seg_flip[seg] != 0;
   const int cls = static_cast<int>(tb.seg_class[seg]);
-  const DigitRule rule = (NB == 10) ? make_rule_dec(cls) : make_rule_bin(cls);
+  const DigitRule rule = (NB == 10) ? rule_dec(cls) : make_rule_bin(cls);
   // absolute first position of this block's keys in every packet
   for (int p = tid; p < NB; p += BLOCK)
     s_gb[p] = tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s + (b - first)];

@@ -7,7 +7,7 @@
 
 #include <cstdint>
 
-#include "../../include/hsort.h"
+#include "hsort.h"
 
 namespace hs {
 

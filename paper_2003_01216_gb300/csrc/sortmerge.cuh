@@ -436,10 +436,12 @@ __global__ void k_corank(const K* __restrict__ ku, const K* __restrict__ kw, Mer
 
 // ---------------------------------------------------------------------------
 // Merge pass r, step 2 -- k_merge: persistent CTAs; each walks merge blocks
-// blockIdx.x, +gridDim.x, ...  Two shared-memory stages: while block k is
-// merged out of one, warp 0 has the bulk-copy engine fill the other with
-// block k+1's A and B windows; block k+2's record is fetched one block ahead.
-// The merged block is staged back into its own stage and leaves by bulk store.
+// blockIdx.x, +gridDim.x, ...  Two input stages: while block k is merged out
+// of one, warp 0 has the bulk-copy engine fill the other with block k+1's A
+// and B windows; block k+2's record is fetched one block ahead.  The merged
+// block is staged in one of two output buffers and leaves by bulk store; the
+// previous block's store has a whole block's time to read the other buffer,
+// so the outputs can be staged without waiting for the inputs to be released.
 // ---------------------------------------------------------------------------
 template <class K, bool HAS_V>
 __device__ __forceinline__ void merge_issue(const MergeRec& rec, K* rk, uint32_t* rv, uint64_t* bar, const K* ku,
@@ -476,11 +478,25 @@ __host__ __device__ constexpr size_t merge_stage_bytes(int tile) {
          (HAS_V ? ((region_elems(tile) * 4 + 127) & ~size_t(127)) : 0);
 }
 
+// Output staging: 4-byte keys without values stage the merged block in one of
+// two separate output buffers (4 buffers of 15 KB still fit three CTAs per
+// SM); wider elements stage it back into the stage they were merged from,
+// which costs one more CTA barrier but keeps two CTAs per SM.
+template <class K, bool HAS_V>
+__host__ __device__ constexpr bool separate_out() {
+  return !HAS_V && sizeof(K) == 4;
+}
+template <class K, bool HAS_V>
+__host__ __device__ constexpr int merge_buffers() {
+  return separate_out<K, HAS_V>() ? 4 : 2;
+}
+
 template <class K, bool HAS_V, int BLOCK, int IPT>
-__global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_merge(K* ku, uint32_t* vu, K* kw, uint32_t* vw,
+__global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_merge(K* ku, uint32_t* vu, K* kw, uint32_t* vw,
                                                                  const MergeRec* __restrict__ recs, uint32_t npk,
                                                                  Tables tb) {
   constexpr int TILE = BLOCK * IPT;
+  constexpr bool SEP = separate_out<K, HAS_V>();
   constexpr size_t KB = (region_elems(TILE) * sizeof(K) + 127) & ~size_t(127);
   constexpr size_t SB = merge_stage_bytes<K, HAS_V>(TILE);
   extern __shared__ __align__(128) unsigned char s_raw[];
@@ -511,11 +527,13 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_me
     unsigned char* st_cur = s_raw + s * SB;
     unsigned char* st_nxt = s_raw + (s ^ 1) * SB;
     if (wid == 0) {
-      if (lane == 0) {
-        bulk_wait_read0();  // the store staged in the other stage has read it
-        fence_proxy_async();
+      if constexpr (!SEP) {
+        if (lane == 0) {
+          bulk_wait_read0();  // the store staged in the other stage has read it
+          fence_proxy_async();
+        }
+        __syncwarp();
       }
-      __syncwarp();
       merge_issue<K, HAS_V>(nxt, reinterpret_cast<K*>(st_nxt), reinterpret_cast<uint32_t*>(st_nxt + KB),
                             &s_bar[s ^ 1], ku, vu, kw, vw, lane);
     }
@@ -552,7 +570,10 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_me
       for (int j = 0; j < IPT; ++j)
         if (d + j < cnt) v[j] = (src[j] & 0x10000) ? rv[qb + (src[j] & 0xffff)] : rv[qa + src[j]];
     }
-    __syncthreads();  // every read of the stage is done: stage the outputs in it
+    unsigned char* ob = SEP ? s_raw + (2 + s) * SB : st_cur;
+    if constexpr (!SEP) __syncthreads();  // every read of the stage is done: stage the outputs in it
+    K* okb = reinterpret_cast<K*>(ob);
+    uint32_t* ovb = reinterpret_cast<uint32_t*>(ob + KB);
     K* kd = (srcw ? ku : kw) + cur.out;
     uint32_t* vd = HAS_V ? (srcw ? vu : vw) + cur.out : nullptr;
     const uint32_t ok_ph = phase_of(kd);
@@ -560,15 +581,16 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_me
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       if (d + j < cnt) {
-        rk[ok_ph + d + j] = k[j];
-        if constexpr (HAS_V) rv[ov_ph + d + j] = v[j];
+        okb[ok_ph + d + j] = k[j];
+        if constexpr (HAS_V) ovb[ov_ph + d + j] = v[j];
       }
     }
     fence_proxy_async();
+    if (SEP && tid == 0) bulk_wait_read0();  // the previous block's store has read the other output buffer
     __syncthreads();
     if (wid == 0 && cnt > 0) {
-      store_window(kd, rk + ok_ph, cnt, lane);
-      if constexpr (HAS_V) store_window(vd, rv + ov_ph, cnt, lane);
+      store_window(kd, okb + ok_ph, cnt, lane);
+      if constexpr (HAS_V) store_window(vd, ovb + ov_ph, cnt, lane);
       if (lane == 0) bulk_commit();
     }
     cur = nxt;
