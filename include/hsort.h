@@ -64,8 +64,9 @@ typedef enum { HS_INT32 = 0, HS_UINT32 = 1, HS_UINT64 = 2 } hs_dtype;
 /* Optional knobs.  A NULL hs_opts*, or any zero field, means "default". */
 typedef struct {
   int partition;        /* 10 (default): MSD decimal packets (Sec. 3.4); 256: top-8-bit ablation */
-  int tile;             /* keys per tile of the per-packet sort; 0 = default for the dtype.
-                           Built tiles: see hs_plan_describe */
+  int tile;             /* keys per tile of the per-packet sort; 0 = the built tile for the call
+                           (7936 for 4-byte keys without values, else 3840; see hs_plan_describe).
+                           Any other value returns HS_ERR_UNSUPPORTED */
   int fan_in;           /* runs merged per merge pass: 2 (default) */
   int stop_after;       /* testing: 0 = whole sort; 1 = stop after the packet step
                            (array holds the stable packet layout); 2 = stop after the
@@ -165,8 +166,8 @@ hs_status hs_stream_error(void* stream);
 
 /* Static description of the plan a call would run (no device work). */
 typedef struct {
-  int tile;            /* keys per tile (= keys per merge block) */
-  int part_tile;       /* keys per block of the packet step */
+  int tile;            /* keys per tile of the per-packet sort (= outputs per merge block) */
+  int part_tile;       /* keys per block of the packet step (3840) */
   int merge_passes;    /* merge passes enqueued (worst case for n; passes no packet needs exit at once) */
   int launches;        /* kernel launches enqueued by one call */
   int fan_in;

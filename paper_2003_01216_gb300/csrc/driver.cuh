@@ -15,8 +15,24 @@ namespace hs {
 
 // Fixed shapes of this build.
 constexpr int kBlock = 256;     // threads per CTA of every heavy kernel
-constexpr int kIpt = 15;        // items per thread (odd: blocked shared-memory access is conflict-free)
-constexpr int kTile = kBlock * kIpt;  // keys per tile sort / merge block / packet-step block
+constexpr int kIpt = 15;        // items per thread of the packet step (odd: conflict-free blocked access)
+constexpr int kTile = kBlock * kIpt;  // keys per packet-step block
+
+// Items per thread of the tile sort and the merge passes: 31 for 4-byte keys
+// without values (twice the work per co-rank search and per block, one merge
+// pass fewer), 15 where 31 items and their companions would not fit in
+// registers.  Odd, so blocked shared-memory access is conflict-free.
+template <class K, bool HAS_V>
+constexpr int sort_ipt() {
+  return (sizeof(K) == 4 && !HAS_V) ? 31 : 15;
+}
+template <class K, bool HAS_V>
+constexpr int sort_tile() {
+  return kBlock * sort_ipt<K, HAS_V>();
+}
+inline int sort_tile_for(size_t key_bytes, bool has_vals) {
+  return kBlock * ((key_bytes == 4 && !has_vals) ? 31 : 15);
+}
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -27,6 +43,7 @@ struct Layout {
 };
 
 inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg, int nb) {
+  const size_t stile = sort_tile_for(key_bytes, has_vals);
   Layout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -36,7 +53,7 @@ inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg
   };
   L.max_blocks = static_cast<uint32_t>((n + kTile - 1) / kTile + nseg);
   L.npk = static_cast<uint32_t>(nseg * nb);
-  L.max_units = static_cast<uint32_t>((n + kTile - 1) / kTile + L.npk);
+  L.max_units = static_cast<uint32_t>((n + stile - 1) / stile + L.npk);
   L.keys_w = take(n * key_bytes + 16);
   L.vals_w = take(has_vals ? n * 4 + 16 : 0);
   L.seg_off = take((nseg + 1) * 8);
@@ -76,9 +93,9 @@ inline Tables make_tables(char* base, const Layout& L, uint32_t* err) {
   return t;
 }
 
-// Worst-case merge passes for a packet of up to n keys.
-inline int worst_passes(size_t n) {
-  size_t tiles = (n + kTile - 1) / kTile;
+// Worst-case merge passes for a packet of up to n keys, sorted in tiles of `tile`.
+inline int worst_passes(size_t n, size_t tile) {
+  size_t tiles = (n + tile - 1) / tile;
   int p = 0;
   while ((static_cast<size_t>(1) << p) < tiles) ++p;
   return p;
@@ -102,11 +119,12 @@ inline size_t hist_smem() {  // two stages of keys
 }
 template <class K, bool HAS_V>
 inline size_t sort_smem() {  // one region of keys (and values)
-  return merge_stage_bytes<K, HAS_V>(kTile);
+  return merge_stage_bytes<K, HAS_V>(sort_tile<K, HAS_V>());
 }
 template <class K, bool HAS_V>
-inline size_t merge_smem() {  // two input stages (+ two output buffers for 4-byte keys)
-  return merge_buffers<K, HAS_V>() * merge_stage_bytes<K, HAS_V>(kTile);
+inline size_t merge_smem() {  // two input stages (+ two output buffers when they fit)
+  constexpr int T = sort_tile<K, HAS_V>();
+  return merge_buffers<K, HAS_V, T>() * merge_stage_bytes<K, HAS_V>(T);
 }
 
 template <class Kern>
@@ -178,7 +196,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     static int grid = 0;
     if (!grid) grid = persistent_grid(k_pkt<NB>, 256, 0);
     lc.begin("pkt");
-    k_pkt<NB><<<grid, 256, 0, st>>>(nseg32, kTile, tb);
+    k_pkt<NB><<<grid, 256, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
     HS_TRY(lc.end());
   }
   lc.begin("scan_units");
@@ -204,7 +222,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     {
       static int grid = 0;
       const size_t smem = sort_smem<K, HAS_V>();
-      auto kern = k_tilesort<K, HAS_V, kBlock, kIpt>;
+      auto kern = k_tilesort<K, HAS_V, kBlock, sort_ipt<K, HAS_V>()>;
       if (!grid) grid = persistent_grid(kern, kBlock, smem);
       lc.begin("tilesort");
       const bool stuck = (o.debug_flags & 1) != 0;
@@ -219,12 +237,12 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     } else {
       static int mgrid = 0, cgrid = 0;
       const size_t smem = merge_smem<K, HAS_V>();
-      auto mk = k_merge<K, HAS_V, kBlock, kIpt>;
-      auto ck = k_corank<K, kTile>;
+      auto mk = k_merge<K, HAS_V, kBlock, sort_ipt<K, HAS_V>()>;
+      auto ck = k_corank<K, sort_tile<K, HAS_V>()>;
       if (!mgrid) mgrid = persistent_grid(mk, kBlock, smem);
       if (!cgrid) cgrid = persistent_grid(ck, 256, 0);
       MergeRec* recs = reinterpret_cast<MergeRec*>(ws + L.recs);
-      const int P = worst_passes(n);
+      const int P = worst_passes(n, sort_tile<K, HAS_V>());
       for (int r = 1; r <= P; ++r) {
         lc.begin("corank");
         ck<<<cgrid, 256, 0, st>>>(keys, kw, recs, L.npk, r, tb);

@@ -98,7 +98,7 @@ hs_status check_opts(const hs_opts* opts, hs_opts* o) {
   if (opts) d = *opts;
   if (d.partition == 0) d.partition = 10;
   if (d.partition != 10 && d.partition != 256) return HS_ERR_INVALID;
-  if (d.tile != 0 && d.tile != kTile) return HS_ERR_UNSUPPORTED;
+  if (d.tile != 0 && d.tile != kBlock * 15 && d.tile != kBlock * 31) return HS_ERR_UNSUPPORTED;
   if (d.fan_in != 0 && d.fan_in != 2) return HS_ERR_UNSUPPORTED;
   if (d.stop_after < 0 || d.stop_after > 2) return HS_ERR_INVALID;
   *o = d;
@@ -112,6 +112,7 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
   HS_TRY(check_opts(opts, &o));
   if (n >= (1ull << 32) || nseg >= (1ull << 24)) return HS_ERR_INVALID;
   if (n > 0 && !keys) return HS_ERR_INVALID;
+  if (o.tile != 0 && o.tile != sort_tile_for(key_bytes(dt), vals != nullptr)) return HS_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (n == 0 && !offs) {
     if (o.d_packet_offsets_out) {
@@ -168,8 +169,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 size_t workspace_bytes(size_t kb, size_t n, bool has_vals, size_t nseg, int nb) {
   return make_layout(kb, n, has_vals, nseg, nb).total;
 }
-int plan_passes(size_t n) { return worst_passes(n); }
-int plan_tile() { return kTile; }
+int plan_passes(size_t n, size_t tile) { return worst_passes(n, tile); }
 
 }  // namespace hs
 
@@ -282,12 +282,11 @@ hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, 
   if (!out || (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64)) return HS_ERR_INVALID;
   hs_opts o;
   HS_TRY(check_opts(opts, &o));
-  (void)has_vals;
   (void)nseg;
-  out->tile = kTile;
+  out->tile = sort_tile_for(key_bytes(dtype), has_vals != 0);
   out->part_tile = kTile;
   out->fan_in = 2;
-  out->merge_passes = (n == 0) ? 0 : worst_passes(n);
+  out->merge_passes = (n == 0) ? 0 : worst_passes(n, static_cast<size_t>(out->tile));
   // seg_plan, hist (x2 for int32), finalize, fold, 3 scan kernels, pkt, scan_units, scatter,
   // tilesort, 2 per merge pass
   int l = 1 + (dtype == HS_INT32 ? 2 : 1) + 1 + 1 + 3 + 1 + 1 + 1;

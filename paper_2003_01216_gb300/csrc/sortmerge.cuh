@@ -96,42 +96,51 @@ __device__ __forceinline__ void cas_keys(K& a, K& b) {
   b = hi;
 }
 
-// Batcher's odd-even merge sort network over 16 slots: the 63 comparators
-// are listed at compile time and expanded by a fold expression, so every
-// register index is a constant.  N <= 16 keys are sorted; unused slots hold
-// the largest key and their comparators fold away.  Keys only: not stable,
-// which does not matter for keys alone.
+// Batcher's odd-even merge sort network over M = 16 or 32 slots: the
+// comparators are listed at compile time and expanded by a fold expression,
+// so every register index is a constant.  N <= M keys are sorted; unused
+// slots hold the largest key and their comparators fold away.  Keys only:
+// not stable, which does not matter for keys alone.
 struct Comparator {
   int a, b;
 };
-constexpr int kBatcher16 = 63;
-struct Batcher16List {
-  Comparator c[kBatcher16];
+template <int M>
+struct BatcherList {
+  Comparator c[M == 16 ? 63 : 191];
 };
-constexpr Batcher16List make_batcher16() {
-  Batcher16List l{};
+template <int M>
+constexpr int batcher_count() {
+  return M == 16 ? 63 : 191;
+}
+template <int M>
+constexpr BatcherList<M> make_batcher() {
+  BatcherList<M> l{};
   int n = 0;
-  for (int p = 1; p < 16; p <<= 1)
+  for (int p = 1; p < M; p <<= 1)
     for (int kk = p; kk >= 1; kk >>= 1)
-      for (int j = kk % p; j + kk < 16; j += 2 * kk)
+      for (int j = kk % p; j + kk < M; j += 2 * kk)
         for (int i = 0; i < kk; ++i)
           if ((i + j) / (2 * p) == (i + j + kk) / (2 * p)) l.c[n++] = Comparator{i + j, i + j + kk};
   return l;
 }
-constexpr Batcher16List kB16 = make_batcher16();
-static_assert(kB16.c[kBatcher16 - 1].b != 0, "63 comparators");
+template <int M>
+struct Batcher {
+  static constexpr BatcherList<M> list = make_batcher<M>();
+};
+static_assert(Batcher<16>::list.c[62].b != 0 && Batcher<32>::list.c[190].b != 0, "comparator counts");
 
-template <class K, int... I>
-__device__ __forceinline__ void apply_b16(K (&t)[16], std::integer_sequence<int, I...>) {
-  (cas_keys(t[kB16.c[I].a], t[kB16.c[I].b]), ...);
+template <int M, class K, int... I>
+__device__ __forceinline__ void apply_batcher(K (&t)[M], std::integer_sequence<int, I...>) {
+  (cas_keys(t[Batcher<M>::list.c[I].a], t[Batcher<M>::list.c[I].b]), ...);
 }
 template <int N, class K>
 __device__ __forceinline__ void network_sort(K (&k)[N]) {
-  static_assert(N <= 16, "network over at most 16 keys");
-  K t[16];
+  static_assert(N <= 32, "network over at most 32 keys");
+  constexpr int M = N <= 16 ? 16 : 32;
+  K t[M];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) t[i] = (i < N) ? k[i] : KT<K>::maxv();
-  apply_b16(t, std::make_integer_sequence<int, kBatcher16>{});
+  for (int i = 0; i < M; ++i) t[i] = (i < N) ? k[i] : KT<K>::maxv();
+  apply_batcher<M>(t, std::make_integer_sequence<int, batcher_count<M>()>{});
 #pragma unroll
   for (int i = 0; i < N; ++i) k[i] = t[i];
 }
@@ -478,17 +487,17 @@ __host__ __device__ constexpr size_t merge_stage_bytes(int tile) {
          (HAS_V ? ((region_elems(tile) * 4 + 127) & ~size_t(127)) : 0);
 }
 
-// Output staging: 4-byte keys without values stage the merged block in one of
-// two separate output buffers (4 buffers of 15 KB still fit three CTAs per
-// SM); wider elements stage it back into the stage they were merged from,
-// which costs one more CTA barrier but keeps two CTAs per SM.
-template <class K, bool HAS_V>
+// Output staging: when four stage-sized buffers fit in 64 KB, the merged
+// block is staged in one of two separate output buffers; otherwise it is
+// staged back into the stage it was merged from, which costs one more CTA
+// barrier but keeps more CTAs per SM.
+template <class K, bool HAS_V, int TILE>
 __host__ __device__ constexpr bool separate_out() {
-  return !HAS_V && sizeof(K) == 4;
+  return 4 * merge_stage_bytes<K, HAS_V>(TILE) <= 64 * 1024;
 }
-template <class K, bool HAS_V>
+template <class K, bool HAS_V, int TILE>
 __host__ __device__ constexpr int merge_buffers() {
-  return separate_out<K, HAS_V>() ? 4 : 2;
+  return separate_out<K, HAS_V, TILE>() ? 4 : 2;
 }
 
 template <class K, bool HAS_V, int BLOCK, int IPT>
@@ -496,7 +505,7 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_me
                                                                  const MergeRec* __restrict__ recs, uint32_t npk,
                                                                  Tables tb) {
   constexpr int TILE = BLOCK * IPT;
-  constexpr bool SEP = separate_out<K, HAS_V>();
+  constexpr bool SEP = separate_out<K, HAS_V, TILE>();
   constexpr size_t KB = (region_elems(TILE) * sizeof(K) + 127) & ~size_t(127);
   constexpr size_t SB = merge_stage_bytes<K, HAS_V>(TILE);
   extern __shared__ __align__(128) unsigned char s_raw[];

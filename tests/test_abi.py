@@ -65,21 +65,22 @@ def test_host_side_rejections():
     assert lib.hs_sort_keys_host(0, None, 5, None, None) == N.HS_ERR_INVALID
 
 
-@pytest.mark.parametrize("n", [1, 3839, 3840, 3841, 1 << 20, 1 << 28])
+@pytest.mark.parametrize("n", [1, 3839, 3840, 3841, 7935, 7936, 7937, 1 << 20, 1 << 28])
 def test_plan_describe(n):
     import math
 
     import paper_2003_01216_gb300 as hs
-    p = hs.plan(N.HS_INT32, n)
-    tile = p["tile"]
-    assert tile == 256 * 15
-    tiles = -(-n // tile)
-    passes = 0 if tiles <= 1 else math.ceil(math.log2(tiles))
-    assert p["merge_passes"] == passes
-    # seg_plan, 2 histogram passes (int32), finalize, fold, 3 scan kernels, packet offsets,
-    # tile prefix, scatter, tile sort, 2 per merge pass
-    assert p["launches"] == 12 + 2 * passes
-    assert hs.plan(N.HS_UINT64, n)["launches"] == 11 + 2 * passes
+    for dtype, has_vals, tile in [(N.HS_INT32, False, 256 * 31), (N.HS_UINT32, False, 256 * 31),
+                                  (N.HS_INT32, True, 256 * 15), (N.HS_UINT64, False, 256 * 15),
+                                  (N.HS_UINT64, True, 256 * 15)]:
+        p = hs.plan(dtype, n, has_vals)
+        assert p["tile"] == tile and p["part_tile"] == 256 * 15
+        tiles = -(-n // tile)
+        passes = 0 if tiles <= 1 else math.ceil(math.log2(tiles))
+        assert p["merge_passes"] == passes
+        # seg_plan, histogram (+ flipped-image histogram for int32), finalize, fold, 3 scan
+        # kernels, packet offsets, tile prefix, scatter, tile sort, 2 per merge pass
+        assert p["launches"] == (12 if dtype == N.HS_INT32 else 11) + 2 * passes
 
 
 def test_workspace_size_grows_with_n():

@@ -12,8 +12,15 @@ from paper_2003_01216_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TILE = hs.plan(0, 1 << 20)["tile"]  # keys per tile, merge block and packet-step block
-SIZES = [1, 2, 100, TILE - 1, TILE, TILE + 1, 3 * TILE + 123, 65536 + 17, 300_001]
+TILE = hs.plan(0, 1 << 20)["tile"]                    # int32 keys: keys per tile and merge block
+TILE_PAIRS = hs.plan(0, 1 << 20, has_vals=True)["tile"]  # pairs (and 64-bit keys)
+PART = hs.plan(0, 1 << 20)["part_tile"]                # keys per packet-step block
+SIZES = sorted({1, 2, 100, TILE - 1, TILE, TILE + 1, PART - 1, PART, PART + 1, 3 * TILE + 123, 65536 + 17,
+                300_001})
+
+
+def tile_of(keys, has_vals):
+    return hs.plan(hs.dtype_code(__import__("torch").from_numpy(keys[:1])), 1 << 20, has_vals=has_vals)["tile"]
 DISTS = ["uniform31", "uniform1e9", "zipf", "sorted", "reverse", "equal", "distinct16", "int32full",
          "three_digit", "uniform32", "uniform64", "distinct2p24"]
 
@@ -48,16 +55,18 @@ def test_partition_stage(oracle, dist, nb):
 @pytest.mark.parametrize("dist", ["uniform1e9", "zipf", "reverse", "distinct16", "uniform64", "distinct2p24"])
 def test_tilesort_stage(oracle, dist, nb):
     # packet step + tile sort: every tile of every packet sorted on its own
-    for n in (TILE + 1, 3 * TILE + 123, 300_001):
+    for n in (TILE + 1, TILE_PAIRS + 1, 3 * TILE + 123, 300_001):
         keys = I.generate(dist, n, seed=2)
         vals = I.index_values(n)
         lk, lv, off = oracle.partition(keys, vals, nb)
-        ek, ev = oracle.tile_sort(lk, off, TILE, lv)
+        ek, ev = oracle.tile_sort(lk, off, tile_of(keys, True), lv)
         gk, gv, _, st = run(keys, vals, nb, stop_after=2)
         assert st == 0
         assert_equal(gk, ek, f"tile-sorted keys {dist} n={n}")
         assert_equal(gv, ev, f"tile-sorted values {dist} n={n}")
+        ek, _ = oracle.tile_sort(lk, off, tile_of(keys, False))
         gk, _, _, st = run(keys, None, nb, stop_after=2)
+        assert st == 0
         assert_equal(gk, ek, f"tile-sorted keys (keys only) {dist} n={n}")
 
 
