@@ -8,7 +8,9 @@
 #include "hsort.h"
 #include "common.cuh"
 #include "partition.cuh"
-#include "sortmerge.cuh"
+#include "blockmerge.cuh"
+#include "merge.cuh"
+#include "tilesort.cuh"
 #include "runtime.h"
 
 namespace hs {

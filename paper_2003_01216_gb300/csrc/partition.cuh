@@ -30,7 +30,7 @@
 #include "async.cuh"
 #include "common.cuh"
 #include "scan.cuh"
-#include "sortmerge.cuh"
+#include "blockmerge.cuh"
 
 namespace hs {
 

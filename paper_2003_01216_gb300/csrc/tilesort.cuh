@@ -1,0 +1,130 @@
+// The tile sort: every tile of every packet sorted by one CTA (see
+// blockmerge.cuh for the layout and the pieces it shares with the merge).
+#pragma once
+#include "blockmerge.cuh"
+
+namespace hs {
+
+// ---------------------------------------------------------------------------
+// k_tilesort
+// ---------------------------------------------------------------------------
+template <class K, bool HAS_V, int BLOCK, int IPT>
+__global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, const uint32_t* __restrict__ vw, K* ku,
+                                                     uint32_t* vu, K* kw_out, uint32_t* vw_out, uint32_t npk,
+                                                     int force_w, int debug_stuck, uint64_t limit_ns, Tables tb) {
+  constexpr int TILE = BLOCK * IPT;
+  constexpr int RE = region_elems(TILE);
+  extern __shared__ __align__(128) unsigned char s_raw[];
+  K* rk = reinterpret_cast<K*>(s_raw);
+  uint32_t* rv = reinterpret_cast<uint32_t*>(s_raw + ((RE * sizeof(K) + 127) & ~size_t(127)));
+  __shared__ __align__(8) uint64_t s_bar;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t total = tb.unit_prefix[npk];
+  if (tid == 0) mbar_init(&s_bar, 1);
+  mbar_fence_init();
+  __syncthreads();
+  uint32_t parity = 0;
+  bool failed = false;
+
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t p = find_pkt(tb.unit_prefix, npk, u);
+    const uint32_t up0 = tb.unit_prefix[p], ntiles = tb.unit_prefix[p + 1] - up0;
+    const int passes = ceil_log2(ntiles);
+    const bool to_w = force_w || (passes & 1);
+    const uint64_t beg = tb.pkt_off[p] + static_cast<uint64_t>(u - up0) * TILE;
+    const int cnt = static_cast<int>(min64(TILE, tb.pkt_off[p + 1] - beg));
+    const K* gk = kw + beg;
+    const uint32_t* gv = HAS_V ? vw + beg : nullptr;
+    const uint32_t pk = phase_of(gk);
+    const uint32_t pv = HAS_V ? phase_of(gv) : 0u;
+
+    if (wid == 0) {  // the tile's keys (and values) into the region at their phase
+      if (lane == 0) {
+        bulk_wait_read0();  // the previous tile's bulk store has read the region
+        fence_proxy_async();
+      }
+      __syncwarp();
+      const PendingBulk<K> bk = load_window_singles(rk, pk, gk, cnt, lane);
+      PendingBulk<uint32_t> bv{nullptr, nullptr, 0};
+      if constexpr (HAS_V) bv = load_window_singles(rv, pv, gv, cnt, lane);
+      cp_async_mbar_arrive(&s_bar);
+      __syncwarp();
+      if (lane == 0) {
+        // testing hook: CTA 0 announces 16 bytes that never arrive on its
+        // first tile, so its bounded wait expires
+        const uint32_t extra = (debug_stuck && blockIdx.x == 0 && u == blockIdx.x) ? 16u : 0u;
+        mbar_arrive_expect_tx(&s_bar, bk.bytes + bv.bytes + extra);
+        if (bk.bytes) bulk_g2s(bk.sdst, bk.gsrc, bk.bytes, &s_bar);
+        if (HAS_V && bv.bytes) bulk_g2s(bv.sdst, bv.gsrc, bv.bytes, &s_bar);
+      }
+    }
+    const bool ok = mbar_wait_bounded(&s_bar, parity, tb.err, limit_ns);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    parity ^= 1;
+
+    K k[IPT];
+    uint32_t v[IPT];
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const int i = tid * IPT + j;
+      k[j] = (i < cnt) ? rk[pk + i] : KT<K>::maxv();
+      if constexpr (HAS_V) v[j] = (i < cnt) ? rv[pv + i] : 0u;
+    }
+    if constexpr (HAS_V) transposition_sort<IPT>(k, v);
+    else network_sort<IPT>(k);
+
+    // merge levels: runs of `run` items -> 2 * run, in the region at offset 0
+#pragma unroll 1
+    for (int run = IPT; run < TILE; run <<= 1) {
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        rk[tid * IPT + j] = k[j];
+        if constexpr (HAS_V) rv[tid * IPT + j] = v[j];
+      }
+      __syncthreads();
+      const int tpg = (2 * run) / IPT;
+      const int a0 = (tid / tpg) * 2 * run;
+      const int diag = (tid % tpg) * IPT;
+      const K* sA = rk + a0;
+      const K* sB = rk + a0 + run;
+      const int i = corank_smem(sA, run, sB, run, diag);
+      int src[IPT];
+      serial_merge<K, IPT, true, HAS_V>(sA, i, run, sB, diag - i, run, IPT, k, src);
+      if constexpr (HAS_V) {
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) v[j] = (src[j] & 0x10000) ? rv[a0 + run + (src[j] & 0xffff)] : rv[a0 + src[j]];
+      }
+    }
+    // blocked registers -> region at the destination's phase -> bulk store
+    K* kd = (to_w ? kw_out : ku) + beg;
+    uint32_t* vd = HAS_V ? (to_w ? vw_out : vu) + beg : nullptr;
+    const uint32_t ok_ph = phase_of(kd);
+    const uint32_t ov_ph = HAS_V ? phase_of(vd) : 0u;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const int i = tid * IPT + j;
+      if (i < cnt) {
+        rk[ok_ph + i] = k[j];
+        if constexpr (HAS_V) rv[ov_ph + i] = v[j];
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (wid == 0) {
+      store_window(kd, rk + ok_ph, cnt, lane);
+      if constexpr (HAS_V) store_window(vd, rv + ov_ph, cnt, lane);
+      if (lane == 0) bulk_commit();
+    }
+  }
+  // a copy may still be in flight into the region: give it a bounded chance
+  // to land before the CTA's shared memory is released
+  if (failed) mbar_wait_bounded(&s_bar, parity, tb.err, limit_ns);
+  if (tid == 0) bulk_wait0();
+}
+
+}  // namespace hs
