@@ -31,7 +31,10 @@ WORKLOADS = {
     # name: (dist, n, has_vals)
     "plain": ("uniform31", 268_435_456, False),
     "pairs": ("uniform64", 134_217_728, True),
+    # 10,000 int32 segments, lengths log-uniform in [16, 2^20] (n is the resulting total)
+    "batch": ("uniform31", 0, False),
 }
+BATCH_SEGMENTS, BATCH_LO, BATCH_HI = 10_000, 16, 1 << 20
 
 
 def load_peaks() -> tuple[float, str]:
@@ -239,6 +242,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 25)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-hi", type=int, default=BATCH_HI)
     args = ap.parse_args()
     rank, world, local = dist_env()
     if world != args.gpus:
@@ -263,6 +267,9 @@ def main():
     dist_name = args.dist or wl_dist
     if args.n:
         n = args.n
+    if args.workload == "batch":
+        run_batch(args, rank, world, dev, dist_name)
+        return
     key_bytes = 8 if I.DTYPE_OF[dist_name] == np.uint64 else 4
     s = key_bytes + (4 if has_vals else 0)
 
@@ -391,6 +398,68 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_batch(args, rank, world, dev, dist_name):
+    """Batched sort (one CUDA-graph launch for all segments) against the plain
+    sort looped over the segments, same stream, same data."""
+    import torch
+
+    import paper_2003_01216_gb300 as hs
+    from paper_2003_01216_gb300 import inputs as I
+
+    off_h = I.batch_offsets(BATCH_SEGMENTS, BATCH_LO, args.batch_hi, seed=0)
+    n = int(off_h[-1])
+    offs = torch.from_numpy(off_h).to(dev)
+    pristine = I.device_generate(dist_name, n, seed=0)
+    work = torch.empty_like(pristine)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        for _ in range(args.warmup):
+            work.copy_(pristine)
+            hs.sort_batch(work, offs, graph=True)
+        if hs.stream_error(st) != 0:
+            raise RuntimeError("device error during warm-up")
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with ClockSampler(dev.index) as clk:
+            barrier(world, dev)
+            torch.cuda.synchronize()
+            l0 = hs.kernel_launches()
+            for i in range(args.steps):
+                work.copy_(pristine)
+                ev[i][0].record(st)
+                hs.sort_batch(work, offs, graph=True)
+                ev[i][1].record(st)
+            torch.cuda.synchronize()
+            launches = hs.kernel_launches() - l0
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        ok = hs.stream_error(st) == 0
+        # the same segments through the plain per-array call, looped on one stream
+        work.copy_(pristine)
+        lo_ = [int(x) for x in off_h]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for s_ in range(BATCH_SEGMENTS):
+            if lo_[s_ + 1] > lo_[s_]:
+                hs.sort_keys(work[lo_[s_]:lo_[s_ + 1]])
+        b.record(st)
+        torch.cuda.synchronize()
+        loop_ms = a.elapsed_time(b)
+    ms_max = reduce_max(ms, world, dev)
+    value = world * n / (ms_max / 1e3)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "batched sort throughput (keys/s): one graph launch over all segments",
+            "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"batch_{BATCH_SEGMENTS}x[{BATCH_LO},{args.batch_hi}]_{dist_name}", "n": n,
+                       "segments": BATCH_SEGMENTS, "lengths": "log-uniform", "seed": 0, "partition": 10},
+            "looped_plain": {"value": n / (loop_ms / 1e3), "unit": "keys/s", "ms": loop_ms,
+                             "calls": BATCH_SEGMENTS},
+            "speedup_vs_looped": loop_ms / ms_max,
+            "gpu_launches": launches, "clocks": clk.summary(), "device_ok": ok,
+        }), flush=True)
 
 
 if __name__ == "__main__":

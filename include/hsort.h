@@ -77,8 +77,14 @@ typedef struct {
   void* d_workspace;    /* optional caller-owned device work space (see hs_workspace_size); when
                            set, the library allocates nothing for this call */
   size_t workspace_bytes;
-  int debug_flags;      /* testing only: bit 0 = one look-back status is never published and
-                           the wait limit is shortened, so the bounded wait expires */
+  int debug_flags;      /* testing only: bit 0 = one bulk copy announces 16 bytes that never
+                           arrive and the wait limit is shortened, so a bounded wait expires */
+  int graph;            /* 1 = capture this call's whole launch sequence in a CUDA graph the
+                           first time these exact arguments (pointers, sizes, options, stream)
+                           are seen, and replay the instantiated graph on later calls.  Needs a
+                           created stream (the legacy default stream cannot be captured) and
+                           per-kernel timing off; otherwise the call runs without a graph.  The
+                           library keeps up to 64 graphs; hs_graph_cache_clear frees them. */
 } hs_opts;
 
 /*
@@ -186,8 +192,12 @@ hs_status hs_timing_enable(int on);
 /* Synchronises the device, returns up to `max` entries, clears the record. */
 hs_status hs_timing_read(hs_kernel_time* out, int max, int* count);
 
+/* Destroy every cached CUDA graph (see hs_opts.graph). */
+hs_status hs_graph_cache_clear(void);
+
 /* Cumulative number of kernel launches this library has enqueued in this
- * process (memsets and copies not counted). */
+ * process (memsets and copies not counted; a graph replay counts the kernels
+ * in the graph). */
 unsigned long long hs_kernel_launches(void);
 
 const char* hs_status_string(hs_status s);

@@ -14,7 +14,7 @@ from . import _native as N
 
 __all__ = [
     "sort_keys", "sort_pairs", "sort_batch", "sort_keys_host", "stream_error", "plan", "workspace_size",
-    "workspace_reserve", "workspace_release", "timing_enable", "timing_read", "kernel_launches", "HsError",
+    "workspace_reserve", "workspace_release", "graph_cache_clear", "timing_enable", "timing_read", "kernel_launches", "HsError",
     "dtype_code",
 ]
 
@@ -45,7 +45,7 @@ def _check_dev(*ts):
             raise ValueError("tensor must be contiguous")
 
 
-def _opts(partition, stop_after, packet_offsets, debug_flags, workspace):
+def _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph=False):
     po = 0
     if packet_offsets is not None:
         _check_dev(packet_offsets)
@@ -55,38 +55,38 @@ def _opts(partition, stop_after, packet_offsets, debug_flags, workspace):
         _check_dev(workspace)
         wp, wb = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     return N.make_opts(partition=partition, stop_after=stop_after, packet_offsets_ptr=po, workspace_ptr=wp,
-                       workspace_bytes=wb, debug_flags=debug_flags)
+                       workspace_bytes=wb, debug_flags=debug_flags, graph=graph)
 
 
 def sort_keys(keys, partition: int = 10, stop_after: int = 0, packet_offsets=None, stream=None,
-              debug_flags: int = 0, workspace=None):
+              debug_flags: int = 0, workspace=None, graph: bool = False):
     """Sort a CUDA tensor of int32/uint32/uint64 keys in place (ascending)."""
     _check_dev(keys)
-    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace)
+    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph)
     N.check(N.lib().hs_sort_keys(dtype_code(keys), keys.data_ptr(), keys.numel(), ctypes.byref(o), _stream(stream)),
             "hs_sort_keys")
     return keys
 
 
 def sort_pairs(keys, vals, partition: int = 10, stop_after: int = 0, packet_offsets=None, stream=None,
-               debug_flags: int = 0, workspace=None):
+               debug_flags: int = 0, workspace=None, graph: bool = False):
     """Stable in-place sort of (key, uint32 value) pairs by key."""
     import torch
     _check_dev(keys, vals)
     if vals.dtype not in (torch.uint32, torch.int32) or vals.numel() != keys.numel():
         raise ValueError("vals must be a uint32 (or int32) tensor as long as keys")
-    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace)
+    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph)
     N.check(N.lib().hs_sort_pairs(dtype_code(keys), keys.data_ptr(), vals.data_ptr(), keys.numel(), 1,
                                   ctypes.byref(o), _stream(stream)), "hs_sort_pairs")
     return keys, vals
 
 
 def sort_batch(keys, offsets, vals=None, partition: int = 10, stop_after: int = 0, packet_offsets=None,
-               stream=None, workspace=None):
+               stream=None, workspace=None, graph: bool = False):
     """Sort every segment [offsets[s], offsets[s+1]) of `keys` on its own.
     offsets: CUDA uint64 (or int64) tensor of nseg + 1 entries."""
     _check_dev(keys, offsets, vals)
-    o = _opts(partition, stop_after, packet_offsets, 0, workspace)
+    o = _opts(partition, stop_after, packet_offsets, 0, workspace, graph)
     nseg = offsets.numel() - 1
     vp = vals.data_ptr() if vals is not None else None
     N.check(N.lib().hs_sort_batch(dtype_code(keys), keys.data_ptr(), vp, offsets.data_ptr(), nseg, keys.numel(),
@@ -138,6 +138,10 @@ def workspace_reserve(nbytes: int, stream=None) -> None:
 
 def workspace_release() -> None:
     N.check(N.lib().hs_workspace_release(), "hs_workspace_release")
+
+
+def graph_cache_clear() -> None:
+    N.check(N.lib().hs_graph_cache_clear(), "hs_graph_cache_clear")
 
 
 def timing_enable(on: bool = True) -> None:

@@ -20,7 +20,7 @@ EXPORTS = [
     "hs_sort_keys", "hs_sort_pairs", "hs_sort_batch", "hs_sort_keys_host", "hs_workspace_size",
     "hs_workspace_reserve", "hs_workspace_release", "hs_stream_error", "hs_plan_describe",
     "hs_timing_enable", "hs_timing_read", "hs_kernel_launches", "hs_status_string", "hs_last_error",
-    "hs_sort_keys_noalloc",
+    "hs_sort_keys_noalloc", "hs_graph_cache_clear",
 ]
 
 
@@ -34,6 +34,7 @@ class HsOpts(ctypes.Structure):
         ("d_workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
         ("debug_flags", ctypes.c_int),
+        ("graph", ctypes.c_int),
     ]
 
 
@@ -78,6 +79,7 @@ def lib() -> ctypes.CDLL:
         L.hs_workspace_size.argtypes = [i, sz, i, sz, p, p]
         L.hs_workspace_reserve.argtypes = [sz, p]
         L.hs_workspace_release.argtypes = []
+        L.hs_graph_cache_clear.argtypes = []
         L.hs_stream_error.argtypes = [p]
         L.hs_plan_describe.argtypes = [i, sz, i, sz, p, p]
         L.hs_timing_enable.argtypes = [i]
@@ -110,6 +112,7 @@ def check(status: int, where: str) -> None:
 
 
 def make_opts(partition: int = 10, stop_after: int = 0, packet_offsets_ptr: int = 0, workspace_ptr: int = 0,
-              workspace_bytes: int = 0, debug_flags: int = 0, tile: int = 0, fan_in: int = 0) -> HsOpts:
+              workspace_bytes: int = 0, debug_flags: int = 0, tile: int = 0, fan_in: int = 0,
+              graph: bool = False) -> HsOpts:
     return HsOpts(partition, tile, fan_in, stop_after, packet_offsets_ptr or None, workspace_ptr or None,
-                  workspace_bytes, debug_flags)
+                  workspace_bytes, debug_flags, int(graph))

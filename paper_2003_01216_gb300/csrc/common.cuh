@@ -184,6 +184,7 @@ struct Tables {
   uint32_t* scan_part;    // scan partials
   uint32_t* seg_neg;      // nseg: segment holds a negative int32 key
   uint32_t* any_neg;      // 1 word: some segment holds a negative int32 key
+  uint32_t* pass_ctl;     // [0]: merge passes the largest packet needs; [r]: merge blocks active in pass r
   uint32_t* seg_cmax;     // nseg * 2: largest block class (identity image, flipped image)
   uint32_t* seg_class;    // nseg: final class (D or B) of the segment
   uint32_t* seg_flip;     // nseg: sign flip in use

@@ -38,9 +38,11 @@ inline int sort_tile_for(size_t key_bytes, bool has_vals) {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+constexpr int kMaxPasses = 64;  // pass-control words (n < 2^32 needs at most 32 passes)
+
 struct Layout {
   size_t keys_w, vals_w, seg_off, blk_prefix, cls_raw, cnt_raw, flat, scan_part, seg_neg, seg_cmax, seg_class,
-      seg_flip, pkt_off, unit_prefix, recs, any_neg, total;
+      seg_flip, pkt_off, unit_prefix, recs, any_neg, pass_ctl, total;
   uint32_t max_blocks, max_units, npk;
 };
 
@@ -72,6 +74,7 @@ inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg
   L.unit_prefix = take((L.npk + 1) * 4);
   L.recs = take((static_cast<size_t>(L.max_units) + 1) * sizeof(MergeRec));
   L.any_neg = take(4);
+  L.pass_ctl = take(kMaxPasses * 4);
   L.total = off;
   return L;
 }
@@ -91,6 +94,7 @@ inline Tables make_tables(char* base, const Layout& L, uint32_t* err) {
   t.pkt_off = reinterpret_cast<uint64_t*>(base + L.pkt_off);
   t.unit_prefix = reinterpret_cast<uint32_t*>(base + L.unit_prefix);
   t.any_neg = reinterpret_cast<uint32_t*>(base + L.any_neg);
+  t.pass_ctl = reinterpret_cast<uint32_t*>(base + L.pass_ctl);
   t.err = err;
   return t;
 }
@@ -157,6 +161,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
   HS_TRY(lc.memset("zero_seg", tb.seg_neg, 0, nseg * 4));
   HS_TRY(lc.memset("zero_cmax", tb.seg_cmax, 0, nseg * 2 * 4));
   HS_TRY(lc.memset("zero_anyneg", tb.any_neg, 0, 4));
+  HS_TRY(lc.memset("zero_passctl", tb.pass_ctl, 0, kMaxPasses * 4));
 
   lc.begin("seg_plan");
   k_seg_plan<<<1, 1024, 0, st>>>(offs, nseg32, n, kTile, tb);
@@ -250,7 +255,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
         ck<<<cgrid, 256, 0, st>>>(keys, kw, recs, L.npk, r, tb);
         HS_TRY(lc.end());
         lc.begin("merge");
-        mk<<<mgrid, kBlock, smem, st>>>(keys, vals, kw, vw, recs, L.npk, tb);
+        mk<<<mgrid, kBlock, smem, st>>>(keys, vals, kw, vw, recs, r, tb);
         HS_TRY(lc.end());
       }
     }

@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "driver.cuh"
@@ -40,6 +41,35 @@ struct TimeRec {
 std::vector<TimeRec> g_times;
 std::vector<cudaEvent_t> g_event_pool;
 std::atomic<unsigned long long> g_launches{0};
+
+// CUDA graphs of whole calls, keyed by every argument that shapes the launch
+// sequence (pointers included: a graph replays with the addresses it saw).
+struct GraphKey {
+  int dev;
+  cudaStream_t st;
+  int dtype;
+  void* keys;
+  uint32_t* vals;
+  const uint64_t* offs;
+  size_t n, nseg;
+  int partition, stop_after, debug;
+  uint64_t* pkt_out;
+  void* ws;
+  size_t ws_bytes;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(dev, st, dtype, keys, vals, offs, n, nseg, partition, stop_after, debug, pkt_out, ws, ws_bytes) <
+           std::tie(o.dev, o.st, o.dtype, o.keys, o.vals, o.offs, o.n, o.nseg, o.partition, o.stop_after, o.debug,
+                    o.pkt_out, o.ws, o.ws_bytes);
+  }
+};
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long kernels = 0;
+  unsigned long long stamp = 0;
+};
+constexpr size_t kMaxGraphs = 64;
+std::map<GraphKey, GraphEntry> g_graphs;
+unsigned long long g_graph_clock = 0;
 
 int current_device() {
   int d = 0;
@@ -135,11 +165,59 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
   } else {
     HS_TRY(grow(g_ws, st, need, &ws));
   }
-  switch (dt) {
-    case HS_INT32: return run_sort_i32(keys, vals, n, nseg, offs, o, ws, err, st);
-    case HS_UINT32: return run_sort_u32(keys, vals, n, nseg, offs, o, ws, err, st);
-    default: return run_sort_u64(keys, vals, n, nseg, offs, o, ws, err, st);
+  auto run = [&]() -> hs_status {
+    switch (dt) {
+      case HS_INT32: return run_sort_i32(keys, vals, n, nseg, offs, o, ws, err, st);
+      case HS_UINT32: return run_sort_u32(keys, vals, n, nseg, offs, o, ws, err, st);
+      default: return run_sort_u64(keys, vals, n, nseg, offs, o, ws, err, st);
+    }
+  };
+  if (!o.graph || st == nullptr || timing_on()) return run();
+  const GraphKey key{current_device(), st, static_cast<int>(dt), keys, vals, offs, n, nseg, o.partition,
+                     o.stop_after, o.debug_flags, o.d_packet_offsets_out, ws,
+                     o.d_workspace ? o.workspace_bytes : need};
+  auto it = g_graphs.find(key);
+  if (it == g_graphs.end()) {
+    if (g_graphs.size() >= kMaxGraphs) {  // evict the least recently used graph
+      auto old = g_graphs.begin();
+      for (auto j = g_graphs.begin(); j != g_graphs.end(); ++j)
+        if (j->second.stamp < old->second.stamp) old = j;
+      cudaGraphExecDestroy(old->second.exec);
+      g_graphs.erase(old);
+    }
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return HS_ERR_CUDA;
+    }
+    const unsigned long long l0 = g_launches.load();
+    hs_status rs = run();
+    const unsigned long long kernels = g_launches.load() - l0;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (rs != HS_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) set_cuda_error(e);
+      return rs != HS_OK ? rs : HS_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return HS_ERR_CUDA;
+    }
+    g_launches.fetch_sub(kernels);  // captured, not launched: counted when replayed
+    it = g_graphs.emplace(key, GraphEntry{exec, kernels, 0}).first;
   }
+  it->second.stamp = ++g_graph_clock;
+  cudaError_t e = cudaGraphLaunch(it->second.exec, st);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return HS_ERR_CUDA;
+  }
+  g_launches.fetch_add(it->second.kernels);
+  return HS_OK;
 }
 
 }  // namespace
@@ -250,6 +328,13 @@ hs_status hs_workspace_release(void) {
       }
     }
   }
+  return HS_OK;
+}
+
+hs_status hs_graph_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& kv : g_graphs) cudaGraphExecDestroy(kv.second.exec);
+  g_graphs.clear();
   return HS_OK;
 }
 

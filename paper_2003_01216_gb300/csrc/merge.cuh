@@ -46,11 +46,17 @@ __device__ __forceinline__ void corank2(const K* __restrict__ A, uint32_t la, co
 template <class K, int TILE>
 __global__ void k_corank(const K* __restrict__ ku, const K* __restrict__ kw, MergeRec* __restrict__ recs,
                          uint32_t npk, int r, Tables tb) {
+  if (static_cast<uint32_t>(r) > tb.pass_ctl[0]) return;  // no packet needs pass r
   const uint32_t total = tb.unit_prefix[npk];
-  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  // warp-uniform trip count: lanes past the end take part in the ballot
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+    const uint32_t u = base + lane;
     MergeGeom g;
     MergeRec rec{0, 0, 0, 0, 0};
-    if (merge_geom<TILE>(tb, npk, u, r, g)) {
+    const bool active = u < total && merge_geom<TILE>(tb, npk, u, r, g);
+    if (active) {
       const bool srcw = ((g.passes - r + 1) & 1) != 0;  // the buffer holding pass r-1
       const K* A = (srcw ? kw : ku) + g.pstart + g.a_start;
       const K* B = A + g.a_len;
@@ -63,7 +69,14 @@ __global__ void k_corank(const K* __restrict__ ku, const K* __restrict__ kw, Mer
       rec.la = i1 - i0;
       rec.lb = g.cnt - rec.la;
     }
-    recs[u] = rec;
+    // active blocks only, packed densely (their order does not matter)
+    const uint32_t mask = __ballot_sync(0xffffffffu, active);
+    if (mask) {
+      uint32_t slot = 0;
+      if (lane == __ffs(mask) - 1) slot = atomicAdd(&tb.pass_ctl[r], __popc(mask));
+      slot = __shfl_sync(0xffffffffu, slot, __ffs(mask) - 1);
+      if (active) recs[slot + __popc(mask & ((1u << lane) - 1u))] = rec;
+    }
   }
 }
 
@@ -126,7 +139,7 @@ __host__ __device__ constexpr int merge_buffers() {
 
 template <class K, bool HAS_V, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_merge(K* ku, uint32_t* vu, K* kw, uint32_t* vw,
-                                                                 const MergeRec* __restrict__ recs, uint32_t npk,
+                                                                 const MergeRec* __restrict__ recs, int r,
                                                                  Tables tb) {
   constexpr int TILE = BLOCK * IPT;
   constexpr bool SEP = separate_out<K, HAS_V, TILE>();
@@ -135,7 +148,7 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_me
   extern __shared__ __align__(128) unsigned char s_raw[];
   __shared__ __align__(8) uint64_t s_bar[2];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint32_t total = tb.unit_prefix[npk];
+  const uint32_t total = tb.pass_ctl[r];  // active merge blocks, packed by k_corank
   const uint32_t G = gridDim.x;
   uint32_t u = blockIdx.x;
   if (u >= total) return;

@@ -347,7 +347,12 @@ __global__ void k_pkt(uint32_t nseg, uint32_t tile, Tables tb) {
     const uint64_t end = (nb_s && p + 1 < NB) ? tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p + 1) * nb_s]
                                                 : tb.seg_off[s + 1];
     tb.pkt_off[idx] = start;
-    tb.unit_prefix[idx] = static_cast<uint32_t>((end - start + tile - 1) / tile);
+    const uint32_t tiles = static_cast<uint32_t>((end - start + tile - 1) / tile);
+    tb.unit_prefix[idx] = tiles;
+    // merge passes this packet needs; the largest is kept for the merge passes
+    const uint32_t passes = tiles <= 1 ? 0u : 32u - __clz(tiles - 1);
+    const uint32_t wmax = __reduce_max_sync(__activemask(), passes);
+    if (wmax && passes == wmax) atomicMax(&tb.pass_ctl[0], wmax);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) tb.pkt_off[m] = tb.seg_off[nseg];
 }

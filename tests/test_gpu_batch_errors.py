@@ -69,8 +69,9 @@ def test_batch_bad_offsets_leave_keys_untouched():
 
 
 def test_bounded_wait_expires_and_context_survives(oracle):
-    # one look-back status is never published (debug flag) and the wait limit
-    # is 2 ms: the waiting block gives up, the call reports HS_ERR_TIMEOUT
+    # one bulk copy of the tile sort announces bytes that never arrive (debug
+    # flag) and the wait limit is 2 ms: the waiting CTA gives up, the call
+    # reports HS_ERR_TIMEOUT
     keys = I.generate("uniform31", 5 * 4096, seed=10)
     _, _, _, st = run(keys, debug_flags=1)
     assert st == HS_TIMEOUT
@@ -114,3 +115,40 @@ def test_streams_do_not_share_work_space(oracle):
     torch.cuda.synchronize()
     assert_equal(ta.cpu().numpy(), oracle.sort(a)[0], "stream 1")
     assert_equal(tb.cpu().numpy(), oracle.sort(b)[0], "stream 2")
+
+
+@pytest.mark.parametrize("nb", [10, 256])
+def test_batch_graph_replay(oracle, nb):
+    # the whole call captured once in a CUDA graph, then replayed on new data
+    off = make_batch(500, 1, 30_000, seed=15)
+    n = int(off[-1])
+    st = torch.cuda.Stream()
+    to = to_dev(off)
+    work = torch.empty(n, dtype=torch.int32, device=dev())
+    for seed in (16, 17, 18):
+        keys = I.generate("uniform31", n, seed=seed)
+        ek, _ = oracle.sort_batch(keys, off, nbuckets=nb)
+        with torch.cuda.stream(st):
+            work.copy_(torch.from_numpy(keys))
+            hs.sort_batch(work, to, partition=nb, graph=True)
+        assert hs.stream_error(st) == 0
+        assert_equal(work.cpu().numpy(), ek, f"graph replay seed {seed}")
+    hs.graph_cache_clear()
+
+
+def test_keys_graph_replay_counts_launches(oracle):
+    st = torch.cuda.Stream()
+    n = 100_000
+    work = torch.empty(n, dtype=torch.uint64, device=dev())
+    launches = []
+    for seed in (20, 21):
+        keys = I.generate("uniform64", n, seed=seed)
+        with torch.cuda.stream(st):
+            work.copy_(torch.from_numpy(keys))
+            l0 = hs.kernel_launches()
+            hs.sort_keys(work, graph=True)
+            launches.append(hs.kernel_launches() - l0)
+        assert hs.stream_error(st) == 0
+        assert_equal(work.cpu().numpy(), oracle.sort(keys)[0], f"graph sort seed {seed}")
+    assert launches[0] == launches[1] == hs.plan(2, n)["launches"]
+    hs.graph_cache_clear()
