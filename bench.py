@@ -33,6 +33,8 @@ WORKLOADS = {
     "pairs": ("uniform64", 134_217_728, True),
     # 10,000 int32 segments, lengths log-uniform in [16, 2^20] (n is the resulting total)
     "batch": ("uniform31", 0, False),
+    # Poisson requests, int32 / uint64, lengths log-uniform in [1024, 2^26]
+    "serve": ("uniform31", 0, False),
 }
 BATCH_SEGMENTS, BATCH_LO, BATCH_HI = 10_000, 16, 1 << 20
 
@@ -243,6 +245,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-hi", type=int, default=BATCH_HI)
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: requests per second")
+    ap.add_argument("--no-serial", action="store_true", help="serve: skip the serial baseline")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if world != args.gpus:
@@ -269,6 +274,9 @@ def main():
         n = args.n
     if args.workload == "batch":
         run_batch(args, rank, world, dev, dist_name)
+        return
+    if args.workload == "serve":
+        run_serve(args, rank, world, dev)
         return
     key_bytes = 8 if I.DTYPE_OF[dist_name] == np.uint64 else 4
     s = key_bytes + (4 if has_vals else 0)
@@ -459,6 +467,41 @@ def run_batch(args, rank, world, dev, dist_name):
                              "calls": BATCH_SEGMENTS},
             "speedup_vs_looped": loop_ms / ms_max,
             "gpu_launches": launches, "clocks": clk.summary(), "device_ok": ok,
+        }), flush=True)
+
+
+def run_serve(args, rank, world, dev):
+    """Serving: Poisson arrivals at --rate for --duration seconds, int32 or
+    uint64 (50/50), lengths log-uniform in [1024, 2^26], 64 GB HBM budget;
+    continuous batching against the serial plain sort of the same stream."""
+    import torch
+
+    from paper_2003_01216_gb300 import serve
+
+    reqs = serve.make_requests(args.rate, args.duration, 1024, 1 << 26, seed=rank)
+    offered = sum(r.n for r in reqs) / args.duration
+    # warm up: the kernels and the caching allocator see each path once
+    warm = serve.make_requests(1000.0, 0.02, 1024, 1 << 22, seed=99)
+    serve.Server(slots=8, seed=99).run(warm)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        barrier(world, dev)
+        st = serve.Server(slots=8, budget_bytes=64 << 30, seed=rank).run(reqs)
+        barrier(world, dev)
+    ser = None if args.no_serial else serve.serial(reqs, seed=rank)
+    keys_s = reduce_max(-st["keys_per_s"], world, dev)  # min over ranks
+    if rank == 0:
+        print(json.dumps({
+            "metric": "serving: keys/s and p50/p99 latency (ms) under Poisson arrivals",
+            "value": world * -keys_s, "unit": "keys/s", "n_gpus": world, "steps": 1, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+u64",
+            "data": "synthetic",
+            "config": {"workload": f"serve_poisson{args.rate:g}_{args.duration:g}s_len[1024,2^26]_i32u64",
+                       "requests": len(reqs), "offered_keys_per_s": offered, "budget_bytes": 64 << 30,
+                       "slots": 8, "small_keys": 1 << 20},
+            "served": st, "serial_plain": ser,
+            "saturated": st["keys_per_s"] < 0.95 * offered,
+            "clocks": clk.summary(),
         }), flush=True)
 
 
