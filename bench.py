@@ -134,11 +134,13 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # byte model (algorithmic bytes, the method's own traffic)
 # --------------------------------------------------------------------------
-def merge_active_keys(pkt_off: np.ndarray, tile: int) -> list[int]:
+def merge_active_keys(pkt_off: np.ndarray, tile: int, fan_in: int = 2) -> list[int]:
     """Keys taking part in each merge pass r = 1.. (packets needing >= r passes)."""
     lens = np.diff(pkt_off.astype(np.int64))
     tiles = (lens + tile - 1) // tile
     passes = np.array([0 if t <= 1 else int(t - 1).bit_length() for t in tiles])
+    if fan_in == 4:
+        passes = (passes + 1) // 2
     P = int(passes.max()) if passes.size else 0
     return [int(lens[passes >= r].sum()) for r in range(1, P + 1)]
 
@@ -219,11 +221,13 @@ def run_reference(args, rank, world):
 
 def workload_config(args, dist, n, has_vals):
     import paper_2003_01216_gb300 as hs
-    tile = hs.plan(0, n)["tile"]
+    code = 2 if dist in ("uniform64", "distinct2p24") else 0
+    pl = hs.plan(code, n, has_vals, fan_in=args.fan_in)
+    tile, fan = pl["tile"], pl["fan_in"]
     return {"workload": f"{args.workload}_{n}_{dist}_{args.partition}pkt", "n": n, "dist": dist,
             "key_dtype": "uint64" if dist in ("uniform64", "distinct2p24") else "int32",
             "values": "uint32 input index" if has_vals else None, "partition": args.partition,
-            "tile": tile, "fan_in": 2, "seed": 0,
+            "tile": tile, "fan_in": fan, "seed": 0,
             "l2": "inputs larger than L2 (>= 1 GiB vs 129 MB); a 1 GiB restore copy between timed steps"}
 
 
@@ -238,6 +242,7 @@ def main():
     ap.add_argument("--workload", default="plain", choices=sorted(WORKLOADS))
     ap.add_argument("--dist", default=None)
     ap.add_argument("--partition", type=int, default=10)
+    ap.add_argument("--fan-in", type=int, default=0, help="runs per merge pass: 2 or 4 (0 = library default)")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--ref-sample", type=int, default=1 << 23)
@@ -295,9 +300,9 @@ def main():
 
     def step():
         if has_vals:
-            hs.sort_pairs(work, vals, partition=args.partition, packet_offsets=pkt)
+            hs.sort_pairs(work, vals, partition=args.partition, packet_offsets=pkt, fan_in=args.fan_in)
         else:
-            hs.sort_keys(work, partition=args.partition, packet_offsets=pkt)
+            hs.sort_keys(work, partition=args.partition, packet_offsets=pkt, fan_in=args.fan_in)
 
     # warm-up (also sizes the work space outside the timed region)
     for _ in range(args.warmup):
@@ -305,7 +310,8 @@ def main():
         step()
     if hs.stream_error() != 0:
         raise RuntimeError("device error during warm-up")
-    plan = hs.plan(hs.dtype_code(work), n, has_vals, 1, args.partition)
+    plan = hs.plan(hs.dtype_code(work), n, has_vals, 1, args.partition, fan_in=args.fan_in)
+    mk = "merge4" if plan["fan_in"] == 4 else "merge"
 
     # timed region: K steps, each bracketed by events on the launching stream
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -341,12 +347,12 @@ def main():
     # roofline of the dominant kernel (merge passes) and of the whole sort
     peak, peak_kind = load_peaks()
     pkt_np = pkt.cpu().numpy()
-    active = merge_active_keys(pkt_np, plan["tile"])
-    merge_launches, merge_ms = per_kernel.get("merge", (0, 0.0))
+    active = merge_active_keys(pkt_np, plan["tile"], plan["fan_in"])
+    merge_launches, merge_ms = per_kernel.get(mk, (0, 0.0))
     merge_bytes = 2 * s * sum(active) * args.steps  # each pass reads and writes its active keys
     achieved = merge_bytes / (merge_ms / 1e3) / 1e9 if merge_ms > 0 else None
     keys_per_launch = sum(active) / max(1, len(active))
-    traffic = ncu_traffic("merge", keys_per_launch)
+    traffic = ncu_traffic(mk, keys_per_launch)
     b_alg = s * n * 1 + 2 * s * n + 2 * s * n + 2 * s * sum(active)  # hist + scatter + tile sort + merges
     whole_gbs = b_alg / (mean_ms / 1e3) / 1e9
     floor_gbs = 2 * s * n / (mean_ms / 1e3) / 1e9
@@ -356,13 +362,13 @@ def main():
     if not has_vals and args.e2e_steps > 0:
         host_pristine = pristine.cpu()
         host = torch.empty_like(host_pristine).pin_memory()
-        hs.sort_keys_host(host.copy_(host_pristine), partition=args.partition)  # warm
+        hs.sort_keys_host(host.copy_(host_pristine), partition=args.partition, fan_in=args.fan_in)  # warm
         e_ms = []
         for _ in range(args.e2e_steps):
             host.copy_(host_pristine)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            hs.sort_keys_host(host, partition=args.partition)
+            hs.sort_keys_host(host, partition=args.partition, fan_in=args.fan_in)
             b.record(stream)
             b.synchronize()
             e_ms.append(a.elapsed_time(b))
@@ -386,7 +392,7 @@ def main():
             "dtype": "int32" if key_bytes == 4 else "u64", "data": "synthetic",
             "config": dict(workload_config(args, dist_name, n, has_vals), merge_passes=len(active),
                            parallelism=f"replicas{world}"),
-            "roofline": {"bound": "hbm", "kernel": "merge", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "hbm", "kernel": mk, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": merge_bytes / max(1, merge_launches),

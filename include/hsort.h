@@ -63,11 +63,16 @@ typedef enum { HS_INT32 = 0, HS_UINT32 = 1, HS_UINT64 = 2 } hs_dtype;
 
 /* Optional knobs.  A NULL hs_opts*, or any zero field, means "default". */
 typedef struct {
-  int partition;        /* 10 (default): MSD decimal packets (Sec. 3.4); 256: top-8-bit ablation */
+  int partition;        /* 10 (default): MSD decimal packets (Sec. 3.4); 256: top-8-bit ablation;
+                           1: no MSD step, the whole array is one packet (the shared-memory
+                           hybrid of Sec. 3.2 alone; ablation) */
   int tile;             /* keys per tile of the per-packet sort; 0 = the built tile for the call
                            (7936 for 4-byte keys without values, else 3840; see hs_plan_describe).
                            Any other value returns HS_ERR_UNSUPPORTED */
-  int fan_in;           /* runs merged per merge pass: 2 (default) */
+  int fan_in;           /* runs merged per merge pass (Fig. 1(b) merges two): 2 (default, also 0)
+                           or 4 (every pass merges groups of four adjacent runs, so half the
+                           passes over memory; same result bit for bit).  Other values
+                           return HS_ERR_UNSUPPORTED */
   int stop_after;       /* testing: 0 = whole sort; 1 = stop after the packet step
                            (array holds the stable packet layout); 2 = stop after the
                            tile sort (every tile of every packet sorted on its own) */
@@ -139,7 +144,7 @@ hs_status hs_sort_keys_host(hs_dtype dtype, void* h_keys, size_t n, const hs_opt
  * library holds it until the process exits.  No cudaMalloc, cudaFree or other
  * allocating call is made.
  *   dtype, d_keys, n, stream  as hs_sort_keys (sorted in place)
- *   partition  10 or 256 (0 = 10)
+ *   partition  10, 256 or 1 (0 = 10)
  * Limits and rules:
  *   - n <= 1,048,576 keys, else HS_ERR_INVALID (hs_last_error says why);
  *   - per-kernel timing (hs_timing_enable) must be off, else HS_ERR_INVALID;
@@ -176,7 +181,7 @@ typedef struct {
   int part_tile;       /* keys per block of the packet step (3840) */
   int merge_passes;    /* merge passes enqueued (worst case for n; passes no packet needs exit at once) */
   int launches;        /* kernel launches enqueued by one call */
-  int fan_in;
+  int fan_in;          /* runs merged per merge pass */
 } hs_plan;
 hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, const hs_opts* opts,
                            hs_plan* out);

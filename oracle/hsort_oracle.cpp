@@ -24,7 +24,8 @@
 // is present; key-value sorts are stable, ties broken by input index; the last
 // part of a packet takes the remainder when T does not divide its length.  A
 // 256-bucket variant (bucket = top 8 significant bits of the largest image) is
-// the ablation partition.
+// the ablation partition; nbuckets = 1 skips the MSD step (the whole array is
+// one packet: the shared-memory hybrid of Sec. 3.2 alone).
 //
 // All arithmetic is integer and exact.
 
@@ -123,6 +124,7 @@ struct Digit {
   int nbuckets = 10;
 
   uint32_t bucket(uint64_t u) const {
+    if (nbuckets == 1) return 0;  // no MSD step: the whole array is one packet
     if (nbuckets == 10) return static_cast<uint32_t>(u / divisor);
     return static_cast<uint32_t>(u >> shift);
   }
@@ -319,7 +321,7 @@ void sort_pairs_impl(K* keys, uint32_t* vals, uint64_t n, int nbuckets, uint32_t
 
 bool valid_args(int dtype, int nbuckets, uint32_t T, int chunk_sort) {
   if (dtype < DT_INT32 || dtype > DT_UINT64) return false;
-  if (nbuckets != 10 && nbuckets != 256) return false;
+  if (nbuckets != 1 && nbuckets != 10 && nbuckets != 256) return false;
   if (T == 0 || (T & (T - 1)) != 0) return false;  // power of two (Sec. 3.2)
   if (chunk_sort != CHUNK_QUICKSORT && chunk_sort != CHUNK_MERGESORT) return false;
   return true;
@@ -377,7 +379,7 @@ void tile_sort_impl(K* keys, uint32_t* vals, const uint64_t* offsets, uint64_t n
 
 // ---------------------------------------------------------------------------
 // C entry points.  dtype: 0 = int32, 1 = uint32, 2 = uint64.  nbuckets: 10
-// (decimal MSD) or 256 (top-8-bit ablation).  T: parts per packet, a power of
+// (decimal MSD), 256 (top-8-bit ablation) or 1 (no MSD step).  T: parts per packet, a power of
 // two.  chunk_sort: 0 = quicksort (Fig. 1(c)), 1 = non-recursive merge sort
 // (Fig. 1(b)).  Every call returns 0 on success, 1 on an invalid argument.
 // Pairs carry uint32 values and need n < 2^32.

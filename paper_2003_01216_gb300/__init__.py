@@ -45,7 +45,7 @@ def _check_dev(*ts):
             raise ValueError("tensor must be contiguous")
 
 
-def _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph=False):
+def _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph=False, fan_in=0):
     po = 0
     if packet_offsets is not None:
         _check_dev(packet_offsets)
@@ -55,38 +55,39 @@ def _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph=F
         _check_dev(workspace)
         wp, wb = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     return N.make_opts(partition=partition, stop_after=stop_after, packet_offsets_ptr=po, workspace_ptr=wp,
-                       workspace_bytes=wb, debug_flags=debug_flags, graph=graph)
+                       workspace_bytes=wb, debug_flags=debug_flags, graph=graph, fan_in=fan_in)
 
 
 def sort_keys(keys, partition: int = 10, stop_after: int = 0, packet_offsets=None, stream=None,
-              debug_flags: int = 0, workspace=None, graph: bool = False):
-    """Sort a CUDA tensor of int32/uint32/uint64 keys in place (ascending)."""
+              debug_flags: int = 0, workspace=None, graph: bool = False, fan_in: int = 0):
+    """Sort a CUDA tensor of int32/uint32/uint64 keys in place (ascending).
+    fan_in: runs merged per merge pass, 2 or 4 (0 = the library default)."""
     _check_dev(keys)
-    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph)
+    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in)
     N.check(N.lib().hs_sort_keys(dtype_code(keys), keys.data_ptr(), keys.numel(), ctypes.byref(o), _stream(stream)),
             "hs_sort_keys")
     return keys
 
 
 def sort_pairs(keys, vals, partition: int = 10, stop_after: int = 0, packet_offsets=None, stream=None,
-               debug_flags: int = 0, workspace=None, graph: bool = False):
+               debug_flags: int = 0, workspace=None, graph: bool = False, fan_in: int = 0):
     """Stable in-place sort of (key, uint32 value) pairs by key."""
     import torch
     _check_dev(keys, vals)
     if vals.dtype not in (torch.uint32, torch.int32) or vals.numel() != keys.numel():
         raise ValueError("vals must be a uint32 (or int32) tensor as long as keys")
-    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph)
+    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in)
     N.check(N.lib().hs_sort_pairs(dtype_code(keys), keys.data_ptr(), vals.data_ptr(), keys.numel(), 1,
                                   ctypes.byref(o), _stream(stream)), "hs_sort_pairs")
     return keys, vals
 
 
 def sort_batch(keys, offsets, vals=None, partition: int = 10, stop_after: int = 0, packet_offsets=None,
-               stream=None, workspace=None, graph: bool = False):
+               stream=None, workspace=None, graph: bool = False, fan_in: int = 0):
     """Sort every segment [offsets[s], offsets[s+1]) of `keys` on its own.
     offsets: CUDA uint64 (or int64) tensor of nseg + 1 entries."""
     _check_dev(keys, offsets, vals)
-    o = _opts(partition, stop_after, packet_offsets, 0, workspace, graph)
+    o = _opts(partition, stop_after, packet_offsets, 0, workspace, graph, fan_in)
     nseg = offsets.numel() - 1
     vp = vals.data_ptr() if vals is not None else None
     N.check(N.lib().hs_sort_batch(dtype_code(keys), keys.data_ptr(), vp, offsets.data_ptr(), nseg, keys.numel(),
@@ -94,7 +95,7 @@ def sort_batch(keys, offsets, vals=None, partition: int = 10, stop_after: int = 
     return keys
 
 
-def sort_keys_host(arr, partition: int = 10, stream=None):
+def sort_keys_host(arr, partition: int = 10, stream=None, fan_in: int = 0):
     """Sort host keys (numpy array or CPU tensor, contiguous) in place through
     the device; returns after the result is back in host memory."""
     import numpy as np
@@ -105,7 +106,7 @@ def sort_keys_host(arr, partition: int = 10, stream=None):
         if not arr.flags.c_contiguous:
             raise ValueError("array must be contiguous")
         ptr, n, code = arr.ctypes.data, arr.size, codes[arr.dtype]
-    o = N.make_opts(partition=partition)
+    o = N.make_opts(partition=partition, fan_in=fan_in)
     N.check(N.lib().hs_sort_keys_host(code, ptr, n, ctypes.byref(o), _stream(stream)), "hs_sort_keys_host")
     return arr
 
@@ -115,9 +116,10 @@ def stream_error(stream=None) -> int:
     return N.lib().hs_stream_error(_stream(stream))
 
 
-def plan(dtype: int, n: int, has_vals: bool = False, nseg: int = 1, partition: int = 10, stop_after: int = 0):
+def plan(dtype: int, n: int, has_vals: bool = False, nseg: int = 1, partition: int = 10, stop_after: int = 0,
+         fan_in: int = 0):
     p = N.HsPlan()
-    o = N.make_opts(partition=partition, stop_after=stop_after)
+    o = N.make_opts(partition=partition, stop_after=stop_after, fan_in=fan_in)
     N.check(N.lib().hs_plan_describe(dtype, n, int(has_vals), nseg, ctypes.byref(o), ctypes.byref(p)),
             "hs_plan_describe")
     return {"tile": p.tile, "part_tile": p.part_tile, "merge_passes": p.merge_passes, "launches": p.launches,

@@ -25,7 +25,8 @@ LIBS = {
     "libhsort.so": ["hsort_abi.cu", "hsort_noalloc.cu", "sort_i32.cu", "sort_u32.cu", "sort_u64.cu"],
     "libhsgen.so": ["gen.cu"],
 }
-HEADERS = ["common.cuh", "async.cuh", "scan.cuh", "partition.cuh", "blockmerge.cuh", "tilesort.cuh", "merge.cuh", "driver.cuh", "runtime.h"]
+HEADERS = ["common.cuh", "async.cuh", "scan.cuh", "partition.cuh", "blockmerge.cuh", "tilesort.cuh", "merge.cuh", "merge4.cuh",
+           "driver.cuh", "runtime.h"]
 
 
 def nvcc() -> str:

@@ -134,8 +134,13 @@ __device__ __forceinline__ DigitRule make_rule_bin(int B) {
 // Montgomery, PLDI 1994).  For u < 2^32 and d = 10^k <= 10^9 the product's
 // error term u * (m - 2^64/d) / 2^64 stays below 2^-32 < 1/d, so the floor is
 // exact; the quotient is at most 9 because u < 10^D.
+// With m = mh * 2^32 + ml, the high 64 bits of u * m are
+// floor((u * mh + floor(u * ml / 2^32)) / 2^32): the dropped low part of u * ml
+// is below 2^32 and cannot carry into bit 64.
 __device__ __forceinline__ uint32_t packet_dec(uint32_t u, const DigitRule& r) {
-  return r.mult ? static_cast<uint32_t>(__umul64hi(static_cast<uint64_t>(u), r.mult)) : u;
+  const uint32_t mh = static_cast<uint32_t>(r.mult >> 32), ml = static_cast<uint32_t>(r.mult);
+  const uint64_t t = static_cast<uint64_t>(u) * mh + __umulhi(u, ml);
+  return r.mult ? static_cast<uint32_t>(t >> 32) : u;
 }
 // Decimal packet of a 64-bit image: how many of the nine thresholds
 // j * 10^(D-1) (j = 1..9) the image reaches.
@@ -191,6 +196,15 @@ struct Tables {
   uint64_t* pkt_off;      // nseg * NB + 1 absolute packet starts
   uint32_t* unit_prefix;  // nseg * NB + 1: first tile of each packet (tile = merge block)
   uint32_t* err;          // device error word
+  int fan_log2;           // log2 of the merge fan-in: 1 (two runs per merge) or 2 (four)
 };
+
+// Merge passes a packet of `tiles` sorted tiles needs at fan-in 2^fan_log2:
+// ceil(log_F(tiles)) = ceil(ceil(log2(tiles)) / fan_log2) for F = 2, 4.
+__host__ __device__ __forceinline__ int passes_of(uint32_t tiles, int fan_log2) {
+  int k = 0;
+  while (k < 32 && (1ull << k) < tiles) ++k;
+  return fan_log2 == 2 ? (k + 1) >> 1 : k;
+}
 
 }  // namespace hs

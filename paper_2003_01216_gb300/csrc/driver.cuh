@@ -2,6 +2,7 @@
 // Included by one translation unit per key type (sort_i32.cu, sort_u32.cu,
 // sort_u64.cu) so the three compile in parallel.
 #pragma once
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -10,6 +11,7 @@
 #include "partition.cuh"
 #include "blockmerge.cuh"
 #include "merge.cuh"
+#include "merge4.cuh"
 #include "tilesort.cuh"
 #include "runtime.h"
 
@@ -38,11 +40,12 @@ inline int sort_tile_for(size_t key_bytes, bool has_vals) {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-constexpr int kMaxPasses = 64;  // pass-control words (n < 2^32 needs at most 32 passes)
+constexpr int kMaxPasses = 64;
+constexpr int kMerge4Spt = 2;  // fan-in-4 merge: chunk slots per tile (average chunk = tile / slots)  // pass-control words (n < 2^32 needs at most 32 passes)
 
 struct Layout {
   size_t keys_w, vals_w, seg_off, blk_prefix, cls_raw, cnt_raw, flat, scan_part, seg_neg, seg_cmax, seg_class,
-      seg_flip, pkt_off, unit_prefix, recs, any_neg, pass_ctl, total;
+      seg_flip, pkt_off, unit_prefix, recs, list, any_neg, pass_ctl, total;
   uint32_t max_blocks, max_units, npk;
 };
 
@@ -72,15 +75,18 @@ inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg
   L.seg_flip = take(nseg * 4);
   L.pkt_off = take((L.npk + 1) * 8);
   L.unit_prefix = take((L.npk + 1) * 4);
-  L.recs = take((static_cast<size_t>(L.max_units) + 1) * sizeof(MergeRec));
+  const size_t slots = static_cast<size_t>(L.max_units) * kMerge4Spt + 1;  // fan-in-4 chunk slots
+  L.recs = take(std::max((static_cast<size_t>(L.max_units) + 1) * sizeof(MergeRec), slots * sizeof(Rec4)));
+  L.list = take(slots * 4);
   L.any_neg = take(4);
   L.pass_ctl = take(kMaxPasses * 4);
   L.total = off;
   return L;
 }
 
-inline Tables make_tables(char* base, const Layout& L, uint32_t* err) {
+inline Tables make_tables(char* base, const Layout& L, uint32_t* err, int fan_log2) {
   Tables t;
+  t.fan_log2 = fan_log2;
   t.seg_off = reinterpret_cast<uint64_t*>(base + L.seg_off);
   t.blk_prefix = reinterpret_cast<uint32_t*>(base + L.blk_prefix);
   t.cls_raw = reinterpret_cast<uint32_t*>(base + L.cls_raw);
@@ -99,13 +105,15 @@ inline Tables make_tables(char* base, const Layout& L, uint32_t* err) {
   return t;
 }
 
-// Worst-case merge passes for a packet of up to n keys, sorted in tiles of `tile`.
-inline int worst_passes(size_t n, size_t tile) {
+// Worst-case merge passes for a packet of up to n keys, sorted in tiles of
+// `tile`, merged `fan_in` runs at a time.
+inline int worst_passes(size_t n, size_t tile, int fan_in = 2) {
   size_t tiles = (n + tile - 1) / tile;
   int p = 0;
   while ((static_cast<size_t>(1) << p) < tiles) ++p;
-  return p;
+  return fan_in == 4 ? (p + 1) / 2 : p;
 }
+inline int fan_log2_of(int fan_in) { return fan_in == 4 ? 2 : 1; }
 
 template <class K, bool HAS_V, int NB>
 inline size_t scatter_smem() {
@@ -115,6 +123,7 @@ inline size_t scatter_smem() {
   b += HAS_V ? kTile * 4 : 0;
   b += NW * (NB + 1) * 4;
   b += ((NB + 2) & ~1) * 4;
+  b += ((NB + 1) & ~1) * 4;
   b += ((NB + 1) & ~1) * 4;
   b += kTile * 2;
   return b;
@@ -126,6 +135,17 @@ inline size_t hist_smem() {  // two stages of keys
 template <class K, bool HAS_V>
 inline size_t sort_smem() {  // one region of keys (and values)
   return merge_stage_bytes<K, HAS_V>(sort_tile<K, HAS_V>());
+}
+// Fan-in-4 merge shape: threads per CTA and CTAs per SM.
+constexpr int kMerge4Block = 256;
+constexpr int kMerge4MinBlocks = 3;
+template <class K, bool HAS_V>
+constexpr int merge4_cmax() {
+  return chunk_max<sort_tile<K, HAS_V>(), kMerge4Spt>();
+}
+template <class K, bool HAS_V>
+inline size_t merge4_smem_for() {  // two stages of the largest chunk and T
+  return merge4_smem<K, HAS_V, merge4_cmax<K, HAS_V>()>();
 }
 template <class K, bool HAS_V>
 inline size_t merge_smem() {  // two input stages (+ two output buffers when they fit)
@@ -151,7 +171,8 @@ template <class K, bool HAS_V, int NB>
 hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
                       char* ws, uint32_t* err, cudaStream_t st) {
   const Layout L = make_layout(sizeof(K), n, HAS_V, nseg, NB);
-  Tables tb = make_tables(ws, L, err);
+  const int fan = o.fan_in == 4 ? 4 : 2;
+  Tables tb = make_tables(ws, L, err, fan_log2_of(fan));
   K* kw = reinterpret_cast<K*>(ws + L.keys_w);
   uint32_t* vw = HAS_V ? reinterpret_cast<uint32_t*>(ws + L.vals_w) : nullptr;
   const uint32_t nseg32 = static_cast<uint32_t>(nseg);
@@ -167,64 +188,77 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
   k_seg_plan<<<1, 1024, 0, st>>>(offs, nseg32, n, kTile, tb);
   HS_TRY(lc.end());
 
-  {
-    static int grid = 0;
-    const size_t smem = hist_smem<K>();
-    auto kern = k_hist<K, NB, kBlock, kIpt>;
-    if (!grid) grid = persistent_grid(kern, kBlock, smem);
-    for (int img = 0; img < (std::is_same<K, int32_t>::value ? 2 : 1); ++img) {
-      lc.begin(img ? "hist_flip" : "hist");
-      kern<<<grid, kBlock, smem, st>>>(keys, nseg32, kTile, img, tb);
+  if constexpr (NB == 1) {
+    // no MSD step (ablation): every segment is one packet; the tile sort
+    // reads the caller's array directly
+    lc.begin("pkt");
+    k_pkt_whole<<<(nseg32 + 255) / 256, 256, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
+    HS_TRY(lc.end());
+    lc.begin("scan_units");
+    k_scan_units<<<1, 1024, 0, st>>>(L.npk, tb);
+    HS_TRY(lc.end());
+  } else {
+    {
+      static int grid = 0;
+      const size_t smem = hist_smem<K>();
+      auto kern = k_hist<K, NB, kBlock, kIpt>;
+      if (!grid) grid = persistent_grid(kern, kBlock, smem);
+      for (int img = 0; img < (std::is_same<K, int32_t>::value ? 2 : 1); ++img) {
+        lc.begin(img ? "hist_flip" : "hist");
+        kern<<<grid, kBlock, smem, st>>>(keys, nseg32, kTile, img, tb);
+        HS_TRY(lc.end());
+      }
+    }
+    lc.begin("finalize");
+    k_finalize<NB><<<(nseg32 + 255) / 256, 256, 0, st>>>(nseg32, tb);
+    HS_TRY(lc.end());
+    {
+      static int grid = 0;
+      if (!grid) grid = persistent_grid(k_fold<NB>, 256, 0);
+      lc.begin("fold");
+      k_fold<NB><<<grid, 256, 0, st>>>(nseg32, tb);
+      HS_TRY(lc.end());
+    }
+    // exclusive scan of the (segment, packet, block) counts: absolute positions
+    const uint32_t* m_ptr = tb.blk_prefix + nseg;  // total blocks (device)
+    lc.begin("scan_reduce");
+    k_scan_reduce<<<kScanChunks, kScanBlock, 0, st>>>(tb.flat, m_ptr, NB, tb.scan_part);
+    HS_TRY(lc.end());
+    lc.begin("scan_partials");
+    k_scan_partials<<<1, kScanBlock, 0, st>>>(tb.scan_part);
+    HS_TRY(lc.end());
+    lc.begin("scan_down");
+    k_scan_down<<<kScanChunks, kScanBlock, 0, st>>>(tb.flat, m_ptr, NB, tb.scan_part);
+    HS_TRY(lc.end());
+    {
+      static int grid = 0;
+      if (!grid) grid = persistent_grid(k_pkt<NB>, 256, 0);
+      lc.begin("pkt");
+      k_pkt<NB><<<grid, 256, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
+      HS_TRY(lc.end());
+    }
+    lc.begin("scan_units");
+    k_scan_units<<<1, 1024, 0, st>>>(L.npk, tb);
+    HS_TRY(lc.end());
+
+    {
+      const size_t smem = scatter_smem<K, HAS_V, NB>();
+      auto kern = k_scatter<K, HAS_V, NB, kBlock, kIpt>;
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        attr = true;
+      }
+      lc.begin("scatter");
+      kern<<<L.max_blocks, kBlock, smem, st>>>(keys, vals, kw, vw, nseg32, kTile, tb);
       HS_TRY(lc.end());
     }
   }
-  lc.begin("finalize");
-  k_finalize<NB><<<(nseg32 + 255) / 256, 256, 0, st>>>(nseg32, tb);
-  HS_TRY(lc.end());
-  {
-    static int grid = 0;
-    if (!grid) grid = persistent_grid(k_fold<NB>, 256, 0);
-    lc.begin("fold");
-    k_fold<NB><<<grid, 256, 0, st>>>(nseg32, tb);
-    HS_TRY(lc.end());
-  }
-  // exclusive scan of the (segment, packet, block) counts: absolute positions
-  const uint32_t* m_ptr = tb.blk_prefix + nseg;  // total blocks (device)
-  lc.begin("scan_reduce");
-  k_scan_reduce<<<kScanChunks, kScanBlock, 0, st>>>(tb.flat, m_ptr, NB, tb.scan_part);
-  HS_TRY(lc.end());
-  lc.begin("scan_partials");
-  k_scan_partials<<<1, kScanBlock, 0, st>>>(tb.scan_part);
-  HS_TRY(lc.end());
-  lc.begin("scan_down");
-  k_scan_down<<<kScanChunks, kScanBlock, 0, st>>>(tb.flat, m_ptr, NB, tb.scan_part);
-  HS_TRY(lc.end());
-  {
-    static int grid = 0;
-    if (!grid) grid = persistent_grid(k_pkt<NB>, 256, 0);
-    lc.begin("pkt");
-    k_pkt<NB><<<grid, 256, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
-    HS_TRY(lc.end());
-  }
-  lc.begin("scan_units");
-  k_scan_units<<<1, 1024, 0, st>>>(L.npk, tb);
-  HS_TRY(lc.end());
-
-  {
-    const size_t smem = scatter_smem<K, HAS_V, NB>();
-    auto kern = k_scatter<K, HAS_V, NB, kBlock, kIpt>;
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-      attr = true;
-    }
-    lc.begin("scatter");
-    kern<<<L.max_blocks, kBlock, smem, st>>>(keys, vals, kw, vw, nseg32, kTile, tb);
-    HS_TRY(lc.end());
-  }
   if (o.stop_after == 1) {
-    HS_TRY(lc.copy("copy_back", keys, kw, n * sizeof(K)));
-    if (HAS_V) HS_TRY(lc.copy("copy_back_v", vals, vw, n * 4));
+    if (NB != 1) {  // with one packet the packet layout is the input itself
+      HS_TRY(lc.copy("copy_back", keys, kw, n * sizeof(K)));
+      if (HAS_V) HS_TRY(lc.copy("copy_back_v", vals, vw, n * 4));
+    }
   } else {
     {
       static int grid = 0;
@@ -234,13 +268,34 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       lc.begin("tilesort");
       const bool stuck = (o.debug_flags & 1) != 0;
       const uint64_t limit_ns = stuck ? 2000000ull : 2000000000ull;  // 2 ms when injected, else 2 s
-      kern<<<grid, kBlock, smem, st>>>(kw, vw, keys, vals, kw, vw, L.npk, o.stop_after == 2 ? 1 : 0, stuck ? 1 : 0,
-                                       limit_ns, tb);
+      const K* ts_k = (NB == 1) ? keys : kw;
+      const uint32_t* ts_v = (NB == 1) ? vals : vw;
+      kern<<<grid, kBlock, smem, st>>>(ts_k, ts_v, keys, vals, kw, vw, L.npk, o.stop_after == 2 ? 1 : 0,
+                                       stuck ? 1 : 0, limit_ns, tb);
       HS_TRY(lc.end());
     }
     if (o.stop_after == 2) {
       HS_TRY(lc.copy("copy_back", keys, kw, n * sizeof(K)));
       if (HAS_V) HS_TRY(lc.copy("copy_back_v", vals, vw, n * 4));
+    } else if (fan == 4) {
+      constexpr int T = sort_tile<K, HAS_V>();
+      static int mgrid = 0, cgrid = 0;
+      const size_t smem = merge4_smem_for<K, HAS_V>();
+      auto mk = k_merge4<K, HAS_V, kMerge4Block, kMerge4MinBlocks, merge4_cmax<K, HAS_V>()>;
+      auto ck = k_bound4<K, T, kMerge4Spt>;
+      if (!mgrid) mgrid = persistent_grid(mk, kMerge4Block, smem);
+      if (!cgrid) cgrid = persistent_grid(ck, 256, 0);
+      Rec4* recs = reinterpret_cast<Rec4*>(ws + L.recs);
+      uint32_t* list = reinterpret_cast<uint32_t*>(ws + L.list);
+      const int P = worst_passes(n, T, 4);
+      for (int r = 1; r <= P; ++r) {
+        lc.begin("bound4");
+        ck<<<cgrid, 256, 0, st>>>(keys, kw, recs, list, L.npk, r, tb);
+        HS_TRY(lc.end());
+        lc.begin("merge4");
+        mk<<<mgrid, kMerge4Block, smem, st>>>(keys, vals, kw, vw, recs, list, r, tb);
+        HS_TRY(lc.end());
+      }
     } else {
       static int mgrid = 0, cgrid = 0;
       const size_t smem = merge_smem<K, HAS_V>();
@@ -269,6 +324,10 @@ template <class K>
 hs_status run_sort(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
                    char* ws, uint32_t* err, cudaStream_t st) {
   K* k = static_cast<K*>(keys);
+  if (o.partition == 1) {
+    if (vals) return run_sort_nb<K, true, 1>(k, vals, n, nseg, offs, o, ws, err, st);
+    return run_sort_nb<K, false, 1>(k, vals, n, nseg, offs, o, ws, err, st);
+  }
   if (o.partition == 256) {
     if (vals) return run_sort_nb<K, true, 256>(k, vals, n, nseg, offs, o, ws, err, st);
     return run_sort_nb<K, false, 256>(k, vals, n, nseg, offs, o, ws, err, st);

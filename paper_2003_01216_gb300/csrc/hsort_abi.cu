@@ -52,14 +52,14 @@ struct GraphKey {
   uint32_t* vals;
   const uint64_t* offs;
   size_t n, nseg;
-  int partition, stop_after, debug;
+  int partition, stop_after, debug, fan_in;
   uint64_t* pkt_out;
   void* ws;
   size_t ws_bytes;
   bool operator<(const GraphKey& o) const {
-    return std::tie(dev, st, dtype, keys, vals, offs, n, nseg, partition, stop_after, debug, pkt_out, ws, ws_bytes) <
-           std::tie(o.dev, o.st, o.dtype, o.keys, o.vals, o.offs, o.n, o.nseg, o.partition, o.stop_after, o.debug,
-                    o.pkt_out, o.ws, o.ws_bytes);
+    return std::tie(dev, st, dtype, keys, vals, offs, n, nseg, partition, stop_after, debug, fan_in, pkt_out, ws,
+                    ws_bytes) < std::tie(o.dev, o.st, o.dtype, o.keys, o.vals, o.offs, o.n, o.nseg, o.partition,
+                                         o.stop_after, o.debug, o.fan_in, o.pkt_out, o.ws, o.ws_bytes);
   }
 };
 struct GraphEntry {
@@ -127,9 +127,10 @@ hs_status check_opts(const hs_opts* opts, hs_opts* o) {
   hs_opts d{};
   if (opts) d = *opts;
   if (d.partition == 0) d.partition = 10;
-  if (d.partition != 10 && d.partition != 256) return HS_ERR_INVALID;
+  if (d.partition != 1 && d.partition != 10 && d.partition != 256) return HS_ERR_INVALID;
   if (d.tile != 0 && d.tile != kBlock * 15 && d.tile != kBlock * 31) return HS_ERR_UNSUPPORTED;
-  if (d.fan_in != 0 && d.fan_in != 2) return HS_ERR_UNSUPPORTED;
+  if (d.fan_in == 0) d.fan_in = 2;
+  if (d.fan_in != 2 && d.fan_in != 4) return HS_ERR_UNSUPPORTED;
   if (d.stop_after < 0 || d.stop_after > 2) return HS_ERR_INVALID;
   *o = d;
   return HS_OK;
@@ -174,7 +175,7 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
   };
   if (!o.graph || st == nullptr || timing_on()) return run();
   const GraphKey key{current_device(), st, static_cast<int>(dt), keys, vals, offs, n, nseg, o.partition,
-                     o.stop_after, o.debug_flags, o.d_packet_offsets_out, ws,
+                     o.stop_after, o.debug_flags, o.fan_in, o.d_packet_offsets_out, ws,
                      o.d_workspace ? o.workspace_bytes : need};
   auto it = g_graphs.find(key);
   if (it == g_graphs.end()) {
@@ -370,11 +371,11 @@ hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, 
   (void)nseg;
   out->tile = sort_tile_for(key_bytes(dtype), has_vals != 0);
   out->part_tile = kTile;
-  out->fan_in = 2;
-  out->merge_passes = (n == 0) ? 0 : worst_passes(n, static_cast<size_t>(out->tile));
+  out->fan_in = o.fan_in;
+  out->merge_passes = (n == 0) ? 0 : worst_passes(n, static_cast<size_t>(out->tile), o.fan_in);
   // seg_plan, hist (x2 for int32), finalize, fold, 3 scan kernels, pkt, scan_units, scatter,
-  // tilesort, 2 per merge pass
-  int l = 1 + (dtype == HS_INT32 ? 2 : 1) + 1 + 1 + 3 + 1 + 1 + 1;
+  // tilesort, 2 per merge pass; without the packet step: seg_plan, pkt, scan_units, tilesort
+  int l = (o.partition == 1) ? 3 : 1 + (dtype == HS_INT32 ? 2 : 1) + 1 + 1 + 3 + 1 + 1 + 1;
   if (o.stop_after != 1) l += 1;
   if (o.stop_after == 0) l += 2 * out->merge_passes;
   out->launches = (n == 0) ? 0 : l;

@@ -63,7 +63,7 @@ using namespace hs;
 extern "C" hs_status hs_sort_keys_noalloc(hs_dtype dtype, void* d_keys, size_t n, int partition, void* stream) {
   if (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64) return HS_ERR_INVALID;
   if (partition == 0) partition = 10;
-  if (partition != 10 && partition != 256) return HS_ERR_INVALID;
+  if (partition != 1 && partition != 10 && partition != 256) return HS_ERR_INVALID;
   if (n > kNoAllocMaxKeys) {
     char msg[128];
     std::snprintf(msg, sizeof(msg), "hs_sort_keys_noalloc: n = %zu exceeds the maximum of %zu keys", n,

@@ -159,16 +159,21 @@ __device__ __forceinline__ void hist_count_block(const K* keysrc, bool from_smem
   const int cls = (NB == 10) ? dec_class(m) : bin_class(m);
   const DigitRule rule = (NB == 10) ? rule_dec(cls) : make_rule_bin(cls);
   if constexpr (NB == 10) {
-    // packed per-thread counters: 6 bits per packet (IPT <= 63)
-    unsigned long long pc = 0;
+    // packed per-thread counters, 4 bits per packet (a thread holds at most
+    // IPT <= 15 keys): packets 0..7 in `lo`, 8..9 in `hi`
+    static_assert(IPT <= 15, "4-bit counters");
+    uint32_t lo = 0, hi = 0;
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
-      if (i < cnt) pc += 1ull << (6 * packet_of<NB>(u[j], rule));
+      const uint32_t p = packet_of<NB>(u[j], rule);
+      const uint32_t inc = (i < cnt) ? (1u << (4 * (p & 7))) : 0u;
+      if (p < 8) lo += inc; else hi += inc;
     }
 #pragma unroll
     for (int q = 0; q < 10; ++q) {
-      const uint32_t c = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>((pc >> (6 * q)) & 63ull));
+      const uint32_t field = ((q < 8 ? lo : hi) >> (4 * (q & 7))) & 15u;
+      const uint32_t c = __reduce_add_sync(0xffffffffu, field);
       if (lane == 0 && c) atomicAdd(&s_cnt[q], c);
     }
   } else {
@@ -350,11 +355,26 @@ __global__ void k_pkt(uint32_t nseg, uint32_t tile, Tables tb) {
     const uint32_t tiles = static_cast<uint32_t>((end - start + tile - 1) / tile);
     tb.unit_prefix[idx] = tiles;
     // merge passes this packet needs; the largest is kept for the merge passes
-    const uint32_t passes = tiles <= 1 ? 0u : 32u - __clz(tiles - 1);
+    const uint32_t passes = static_cast<uint32_t>(passes_of(tiles, tb.fan_log2));
     const uint32_t wmax = __reduce_max_sync(__activemask(), passes);
     if (wmax && passes == wmax) atomicMax(&tb.pass_ctl[0], wmax);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) tb.pkt_off[m] = tb.seg_off[nseg];
+}
+
+// ---------------------------------------------------------------------------
+// k_pkt_whole: no MSD step (ablation): every segment is one packet.
+// ---------------------------------------------------------------------------
+static __global__ void k_pkt_whole(uint32_t nseg, uint32_t tile, Tables tb) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
+    const uint64_t start = tb.seg_off[s], end = tb.seg_off[s + 1];
+    tb.pkt_off[s] = start;
+    const uint32_t tiles = static_cast<uint32_t>((end - start + tile - 1) / tile);
+    tb.unit_prefix[s] = tiles;
+    const uint32_t passes = static_cast<uint32_t>(passes_of(tiles, tb.fan_log2));
+    if (passes) atomicMax(&tb.pass_ctl[0], passes);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) tb.pkt_off[nseg] = tb.seg_off[nseg];
 }
 
 // ---------------------------------------------------------------------------
@@ -417,8 +437,9 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + TILE);        // TILE (pairs)
   uint32_t* s_wc = s_vals + (HAS_V ? TILE : 0);                         // NW * NBX warp counts
   uint32_t* s_bs = s_wc + NW * NBX;                                     // NB + 1 block packet starts
-  uint32_t* s_gb = s_bs + ((NB + 2) & ~1);                              // NB absolute bases
-  uint16_t* s_pk = reinterpret_cast<uint16_t*>(s_gb + ((NB + 1) & ~1)); // TILE packet ids
+  uint32_t* s_gb = s_bs + ((NB + 2) & ~1);                              // NB absolute bases, then deltas
+  uint32_t* s_pe = s_gb + ((NB + 1) & ~1);                              // NB packet ends (absolute)
+  uint16_t* s_pk = reinterpret_cast<uint16_t*>(s_pe + ((NB + 1) & ~1)); // TILE packet ids
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t b = blockIdx.x;
@@ -433,8 +454,10 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
   const int cls = static_cast<int>(tb.seg_class[seg]);
   const DigitRule rule = (NB == 10) ? rule_dec(cls) : make_rule_bin(cls);
   // absolute first position of this block's keys in every packet
-  for (int p = tid; p < NB; p += BLOCK)
+  for (int p = tid; p < NB; p += BLOCK) {
     s_gb[p] = tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s + (b - first)];
+    s_pe[p] = static_cast<uint32_t>(tb.pkt_off[static_cast<size_t>(seg) * NB + p + 1]);
+  }
   __syncthreads();
 
   // load (warp-striped) and compute packets; rank and packet share a register
@@ -488,6 +511,8 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
     s_bs[NB] = run;
   }
   __syncthreads();
+  // staged element e of packet p goes to e + (first position - block start) of p
+  for (int p = tid; p < NB; p += BLOCK) s_gb[p] -= s_bs[p];
   // stage grouped by packet, in input order inside each packet
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
@@ -500,11 +525,10 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
     }
   }
   __syncthreads();
-  const uint64_t* pend = tb.pkt_off + static_cast<size_t>(seg) * NB + 1;
   for (uint32_t e = tid; e < cnt; e += BLOCK) {
     const uint32_t p = s_pk[e];
-    const uint64_t dst = static_cast<uint64_t>(s_gb[p]) + (e - s_bs[p]);
-    if (dst >= pend[p]) {
+    const uint32_t dst = s_gb[p] + e;  // positions < n < 2^32
+    if (dst >= s_pe[p]) {
       atomicOr(tb.err, kErrBounds);
       continue;
     }

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
     const uint32_t p = find_pkt(tb.unit_prefix, npk, u);
     const uint32_t up0 = tb.unit_prefix[p], ntiles = tb.unit_prefix[p + 1] - up0;
-    const int passes = ceil_log2(ntiles);
+    const int passes = passes_of(ntiles, tb.fan_log2);
     const bool to_w = force_w || (passes & 1);
     const uint64_t beg = tb.pkt_off[p] + static_cast<uint64_t>(u - up0) * TILE;
     const int cnt = static_cast<int>(min64(TILE, tb.pkt_off[p + 1] - beg));

@@ -81,6 +81,14 @@ def test_plan_describe(n):
         # seg_plan, histogram (+ flipped-image histogram for int32), finalize, fold, 3 scan
         # kernels, packet offsets, tile prefix, scatter, tile sort, 2 per merge pass
         assert p["launches"] == (12 if dtype == N.HS_INT32 else 11) + 2 * passes
+        # without the MSD step: seg_plan, packet table, tile prefix, tile sort
+        assert hs.plan(dtype, n, has_vals, partition=1)["launches"] == 4 + 2 * passes
+        # fan-in 4: ceil(log4(tiles)) passes, still two launches each
+        p4 = hs.plan(dtype, n, has_vals, fan_in=4)
+        passes4 = 0 if tiles <= 1 else math.ceil(math.log(tiles, 4) - 1e-12)
+        assert p4["fan_in"] == 4 and p4["merge_passes"] == passes4 == (passes + 1) // 2
+        assert p4["launches"] == (12 if dtype == N.HS_INT32 else 11) + 2 * passes4
+        assert p["fan_in"] == 2
 
 
 def test_workspace_size_grows_with_n():

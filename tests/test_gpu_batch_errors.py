@@ -22,9 +22,10 @@ def make_batch(count, lo, hi, seed, empties=True):
     return off
 
 
-@pytest.mark.parametrize("nb", [10, 256])
+@pytest.mark.parametrize("fan", [2, 4])
+@pytest.mark.parametrize("nb", [1, 10, 256])
 @pytest.mark.parametrize("dist", ["uniform31", "zipf", "int32full", "uniform32", "uniform64", "distinct2p24"])
-def test_sort_batch(oracle, dist, nb):
+def test_sort_batch(oracle, dist, nb, fan):
     off = make_batch(300, 1, 20_000, seed=5)
     n = int(off[-1])
     keys = I.generate(dist, n, seed=6)
@@ -32,12 +33,12 @@ def test_sort_batch(oracle, dist, nb):
     ek, ev = oracle.sort_batch(keys, off, vals, nbuckets=nb)
     tk, tv, to = to_dev(keys), to_dev(vals), to_dev(off)
     poff = torch.zeros(300 * nb + 1, dtype=torch.uint64, device=dev())
-    hs.sort_batch(tk, to, tv, partition=nb, packet_offsets=poff)
+    hs.sort_batch(tk, to, tv, partition=nb, packet_offsets=poff, fan_in=fan)
     assert hs.stream_error() == 0
     assert_equal(tk.cpu().numpy(), ek, f"batch keys {dist}")
     assert_equal(tv.cpu().numpy(), ev, f"batch values {dist}")
     tk = to_dev(keys)
-    hs.sort_batch(tk, to, None, partition=nb)
+    hs.sort_batch(tk, to, None, partition=nb, fan_in=fan)
     assert hs.stream_error() == 0
     assert_equal(tk.cpu().numpy(), ek, f"batch keys only {dist}")
     # packet offsets of every segment equal the oracle's, shifted by the segment start
@@ -117,8 +118,9 @@ def test_streams_do_not_share_work_space(oracle):
     assert_equal(tb.cpu().numpy(), oracle.sort(b)[0], "stream 2")
 
 
+@pytest.mark.parametrize("fan", [2, 4])
 @pytest.mark.parametrize("nb", [10, 256])
-def test_batch_graph_replay(oracle, nb):
+def test_batch_graph_replay(oracle, nb, fan):
     # the whole call captured once in a CUDA graph, then replayed on new data
     off = make_batch(500, 1, 30_000, seed=15)
     n = int(off[-1])
@@ -130,7 +132,7 @@ def test_batch_graph_replay(oracle, nb):
         ek, _ = oracle.sort_batch(keys, off, nbuckets=nb)
         with torch.cuda.stream(st):
             work.copy_(torch.from_numpy(keys))
-            hs.sort_batch(work, to, partition=nb, graph=True)
+            hs.sort_batch(work, to, partition=nb, graph=True, fan_in=fan)
         assert hs.stream_error(st) == 0
         assert_equal(work.cpu().numpy(), ek, f"graph replay seed {seed}")
     hs.graph_cache_clear()

@@ -25,14 +25,14 @@ N_PAIRS = 134_217_728
 _cache = {}
 
 
-def gpu_sort(keys, vals=None, nb=10):
+def gpu_sort(keys, vals=None, nb=10, fan_in=0):
     tk = torch.from_numpy(keys).to(dev())
     tv = torch.from_numpy(vals).to(dev()) if vals is not None else None
     off = torch.zeros(nb + 1, dtype=torch.uint64, device=dev())
     if tv is None:
-        hs.sort_keys(tk, partition=nb, packet_offsets=off)
+        hs.sort_keys(tk, partition=nb, packet_offsets=off, fan_in=fan_in)
     else:
-        hs.sort_pairs(tk, tv, partition=nb, packet_offsets=off)
+        hs.sort_pairs(tk, tv, partition=nb, packet_offsets=off, fan_in=fan_in)
     assert hs.stream_error() == 0
     out = (tk.cpu().numpy(), tv.cpu().numpy() if tv is not None else None, off.cpu().numpy())
     del tk, tv
@@ -54,6 +54,10 @@ def test_fullsize_plain_vs_oracle(oracle, dist):
     ek, _, eoff = oracle.sort(keys, None, 10)
     assert_equal(goff, eoff, f"{dist} packet offsets")
     assert_equal(gk, ek, f"{dist} sorted keys")
+    # fan-in 4 merge passes: the same unique sorted output
+    gk4, _, goff4 = gpu_sort(keys, fan_in=4)
+    assert_equal(goff4, eoff, f"{dist} packet offsets (fan-in 4)")
+    assert_equal(gk4, ek, f"{dist} sorted keys (fan-in 4)")
     if dist == "uniform31":
         # 256-bucket ablation: same unique sorted output, its own offsets
         gk2, _, goff2 = gpu_sort(keys, nb=256)
@@ -63,9 +67,10 @@ def test_fullsize_plain_vs_oracle(oracle, dist):
 
 
 @pytest.mark.parametrize("dist", ["sorted", "reverse", "equal", "distinct16"])
-def test_fullsize_plain_closed_form(oracle, dist):
+@pytest.mark.parametrize("fan", [2, 4])
+def test_fullsize_plain_closed_form(oracle, dist, fan):
     keys = host_keys(dist)
-    gk, _, goff = gpu_sort(keys)
+    gk, _, goff = gpu_sort(keys, fan_in=fan)
     _, _, eoff = oracle.partition(keys, None, 10)
     assert_equal(goff, eoff, f"{dist} packet offsets")
     if dist == "sorted" or dist == "equal":
@@ -88,3 +93,7 @@ def test_fullsize_stable_pairs_vs_oracle(oracle, dist):
     assert_equal(goff, eoff, f"{dist} packet offsets")
     assert_equal(gk, ek, f"{dist} pair keys")
     assert_equal(gv, ev, f"{dist} pair values (stable order)")
+    gk, gv, goff = gpu_sort(keys, vals, fan_in=4)
+    assert_equal(goff, eoff, f"{dist} packet offsets (fan-in 4)")
+    assert_equal(gk, ek, f"{dist} pair keys (fan-in 4)")
+    assert_equal(gv, ev, f"{dist} pair values (stable order, fan-in 4)")

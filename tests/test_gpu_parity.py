@@ -33,7 +33,7 @@ def test_device_generator_matches_host(dist):
         assert_equal(d.cpu().numpy(), h, f"device generator {dist} n={n}")
 
 
-@pytest.mark.parametrize("nb", [10, 256])
+@pytest.mark.parametrize("nb", [1, 10, 256])
 @pytest.mark.parametrize("dist", DISTS)
 def test_partition_stage(oracle, dist, nb):
     # the packet step alone: stable layout and packet offsets, bit-exact
@@ -51,7 +51,7 @@ def test_partition_stage(oracle, dist, nb):
         assert_equal(gv, ev, f"packet layout values {dist} n={n}")
 
 
-@pytest.mark.parametrize("nb", [10, 256])
+@pytest.mark.parametrize("nb", [1, 10, 256])
 @pytest.mark.parametrize("dist", ["uniform1e9", "zipf", "reverse", "distinct16", "uniform64", "distinct2p24"])
 def test_tilesort_stage(oracle, dist, nb):
     # packet step + tile sort: every tile of every packet sorted on its own
@@ -70,30 +70,67 @@ def test_tilesort_stage(oracle, dist, nb):
         assert_equal(gk, ek, f"tile-sorted keys (keys only) {dist} n={n}")
 
 
-@pytest.mark.parametrize("nb", [10, 256])
+@pytest.mark.parametrize("fan", [2, 4])
+@pytest.mark.parametrize("nb", [1, 10, 256])
 @pytest.mark.parametrize("dist", DISTS)
-def test_sort_keys(oracle, dist, nb):
+def test_sort_keys(oracle, dist, nb, fan):
     for n in SIZES:
         keys = I.generate(dist, n, seed=3)
         ek, _, eoff = oracle.sort(keys, None, nb)
-        gk, _, goff, st = run(keys, None, nb)
+        gk, _, goff, st = run(keys, None, nb, fan_in=fan)
         assert st == 0
         assert_equal(gk, ek, f"sorted keys {dist} n={n}")
         assert_equal(goff, eoff, f"packet offsets {dist} n={n}")
 
 
-@pytest.mark.parametrize("nb", [10, 256])
+@pytest.mark.parametrize("fan", [2, 4])
+@pytest.mark.parametrize("nb", [1, 10, 256])
 @pytest.mark.parametrize("dist", ["uniform31", "zipf", "equal", "distinct16", "int32full", "uniform32",
                                   "uniform64", "distinct2p24"])
-def test_sort_pairs_stable(oracle, dist, nb):
+def test_sort_pairs_stable(oracle, dist, nb, fan):
     for n in SIZES:
         keys = I.generate(dist, n, seed=4)
         vals = I.index_values(n)
         ek, ev, _ = oracle.sort(keys, vals, nb)
-        gk, gv, _, st = run(keys, vals, nb)
+        gk, gv, _, st = run(keys, vals, nb, fan_in=fan)
         assert st == 0
         assert_equal(gk, ek, f"pair keys {dist} n={n}")
         assert_equal(gv, ev, f"pair values (stable order) {dist} n={n}")
+
+
+@pytest.mark.parametrize("dist", ["uniform31", "zipf", "sorted", "reverse", "equal", "distinct16", "uniform64"])
+def test_fan4_group_shapes(oracle, dist):
+    # one packet (no MSD step), so the run geometry is exact: groups of four
+    # runs, ragged last groups of one, two and three runs, and packets needing
+    # one to three passes of four-way merges; keys and stable pairs
+    sizes = []
+    for tiles in (2, 3, 4, 5, 7, 8, 9, 15, 16, 17, 33, 63, 64, 65):
+        sizes += [tiles * TILE - 1, tiles * TILE + 1]
+    for n in sizes:
+        keys = I.generate(dist, n, seed=40)
+        ek, _, _ = oracle.sort(keys, None, 1)
+        gk, _, _, st = run(keys, None, 1, fan_in=4)
+        assert st == 0
+        assert_equal(gk, ek, f"fan-in 4 keys {dist} n={n}")
+    for n in (2 * TILE_PAIRS + 7, 5 * TILE_PAIRS + 3, 17 * TILE_PAIRS + 1, 70 * TILE_PAIRS + 11):
+        keys = I.generate(dist, n, seed=41)
+        vals = I.index_values(n)
+        ek, ev, _ = oracle.sort(keys, vals, 1)
+        gk, gv, _, st = run(keys, vals, 1, fan_in=4)
+        assert st == 0
+        assert_equal(gk, ek, f"fan-in 4 pair keys {dist} n={n}")
+        assert_equal(gv, ev, f"fan-in 4 pair values {dist} n={n}")
+
+
+def test_fan4_large(oracle):
+    # 2^22 keys in ten packets: up to five four-way passes with multi-chunk groups
+    for dist in ("uniform1e9", "zipf"):
+        keys = I.generate(dist, 1 << 22, seed=42)
+        ek, _, eoff = oracle.sort(keys, None, 10)
+        gk, _, goff, st = run(keys, None, 10, fan_in=4)
+        assert st == 0
+        assert_equal(gk, ek, f"fan-in 4 sorted keys {dist}")
+        assert_equal(goff, eoff, f"fan-in 4 packet offsets {dist}")
 
 
 def test_config1_plain_keys(oracle):

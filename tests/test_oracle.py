@@ -241,10 +241,26 @@ def test_tile_sort_intermediate(oracle):
             np.testing.assert_array_equal(ts[lo:hi], np.sort(lay[lo:hi]))
 
 
+@pytest.mark.parametrize("dist", ["uniform31", "int32full", "uniform64", "distinct16"])
+def test_one_packet_is_the_plain_hybrid(oracle, dist):
+    # nbuckets = 1: no MSD step, the whole array is one packet (Sec. 3.2 alone);
+    # the sorted result is the same as with the MSD step
+    keys = I.generate(dist, 20_000, seed=8)
+    vals = I.index_values(keys.size)
+    lay, lv, off = oracle.partition(keys, vals, 1)
+    np.testing.assert_array_equal(lay, keys)
+    np.testing.assert_array_equal(lv, vals)
+    assert list(off) == [0, keys.size]
+    k1, v1, _ = oracle.sort(keys, vals, 1)
+    k10, v10, _ = oracle.sort(keys, vals, 10)
+    np.testing.assert_array_equal(k1, k10)
+    np.testing.assert_array_equal(v1, v10)
+
+
 def test_invalid_arguments(oracle):
     keys = np.arange(10, dtype=np.int32)
     with pytest.raises(ValueError):
-        oracle.sort(keys, None, 7)          # neither 10 nor 256 packets
+        oracle.sort(keys, None, 7)          # neither 1, 10 nor 256 packets
     with pytest.raises(ValueError):
         oracle.sort(keys, None, 10, T=3)    # T must be a power of two (Sec. 3.2)
 
