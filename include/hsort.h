@@ -79,8 +79,9 @@ typedef struct {
   uint64_t* d_packet_offsets_out; /* optional device array of partition*nseg + 1 uint64:
                            packet p of segment s spans [off[s*partition + p], off[s*partition+p+1])
                            as absolute element positions */
-  void* d_workspace;    /* optional caller-owned device work space (see hs_workspace_size); when
-                           set, the library allocates nothing for this call */
+  void* d_workspace;    /* optional caller-owned device work space (see hs_workspace_size),
+                           256-byte aligned (else HS_ERR_INVALID); when set, the library
+                           allocates nothing for this call */
   size_t workspace_bytes;
   int debug_flags;      /* testing only: bit 0 = one bulk copy announces 16 bytes that never
                            arrive and the wait limit is shortened, so a bounded wait expires */

@@ -241,7 +241,16 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     k_scan_units<<<1, 1024, 0, st>>>(L.npk, tb);
     HS_TRY(lc.end());
 
-    {
+    if constexpr (NB <= 16) {
+      // persistent: bulk copies in and out, ranks from one scan of packed counts
+      static int grid = 0;
+      const size_t smem = ScatterSmallLayout<K, HAS_V, kBlock, kIpt>::bytes;
+      auto kern = k_scatter_small<K, HAS_V, NB, kBlock, kIpt>;
+      if (!grid) grid = persistent_grid(kern, kBlock, smem);
+      lc.begin("scatter");
+      kern<<<grid, kBlock, smem, st>>>(keys, vals, kw, vw, nseg32, kTile, tb);
+      HS_TRY(lc.end());
+    } else {
       const size_t smem = scatter_smem<K, HAS_V, NB>();
       auto kern = k_scatter<K, HAS_V, NB, kBlock, kIpt>;
       static bool attr = false;

@@ -161,7 +161,7 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
   const size_t need = workspace_bytes(key_bytes(dt), n, vals != nullptr, nseg, o.partition);
   char* ws = nullptr;
   if (o.d_workspace) {
-    if (o.workspace_bytes < need) return HS_ERR_INVALID;
+    if (o.workspace_bytes < need || (reinterpret_cast<uintptr_t>(o.d_workspace) & 255u)) return HS_ERR_INVALID;
     ws = static_cast<char*>(o.d_workspace);
   } else {
     HS_TRY(grow(g_ws, st, need, &ws));

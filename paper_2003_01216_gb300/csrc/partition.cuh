@@ -537,4 +537,226 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
   }
 }
 
+// ---------------------------------------------------------------------------
+// k_scatter_small: the stable move for up to 16 packets (the ten decimal
+// packets), persistent CTAs over blocks blockIdx.x, +gridDim.x, ...
+//   * a block's keys (and values) arrive by bulk copy in the CTA's input stage;
+//     thread t takes items t*IPT .. t*IPT+IPT-1 (so input order is thread
+//     order, then item order) and, once every thread holds its items, the next
+//     block's copy is issued into the same stage;
+//   * each thread counts its items per packet in 4-bit fields (its local rank
+//     of every item falls out on the way), and one block-wide scan of those
+//     counts, two packets per 32-bit word, gives every thread its first rank
+//     in every packet: stable ranks without a per-item warp vote;
+//   * every packet's run is staged in shared memory at the 16-byte phase of
+//     its destination and leaves as one bulk store (unaligned ends by plain
+//     stores); a run that would pass its packet's end sets kErrBounds and is
+//     not written.
+// The output buffers must be 16-byte aligned (the work space is 256-byte
+// aligned).
+// ---------------------------------------------------------------------------
+template <class K, bool HAS_V, int BLOCK, int IPT>
+struct ScatterSmallLayout {
+  static constexpr int TILE = BLOCK * IPT;
+  static constexpr size_t SK = (region_elems(TILE) * sizeof(K) + 127) & ~size_t(127);
+  static constexpr size_t SV = HAS_V ? ((region_elems(TILE) * 4 + 127) & ~size_t(127)) : 0;
+  static constexpr int OUTE = TILE + 8 * 16;  // runs padded to their phase: at most 7 extra per run
+  static constexpr size_t OK = (OUTE * sizeof(K) + 127) & ~size_t(127);
+  static constexpr size_t OV = HAS_V ? ((OUTE * 4 + 127) & ~size_t(127)) : 0;
+  static constexpr size_t PREF = BLOCK * 16 * 2;  // u16 first staging position per thread and packet
+  static constexpr size_t bytes = SK + SV + OK + OV + PREF;
+};
+
+template <class K, bool HAS_V, int NB, int BLOCK, int IPT>
+__global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_scatter_small(const K* __restrict__ keys_in,
+                                                            const uint32_t* __restrict__ vals_in,
+                                                            K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                                                            uint32_t nseg, uint32_t part_tile, Tables tb) {
+  static_assert(NB <= 16 && IPT <= 15, "4-bit local counts; 16-bit block counts");
+  using LY = ScatterSmallLayout<K, HAS_V, BLOCK, IPT>;
+  constexpr int NW = BLOCK / kWarp;
+  constexpr int NWORD = (NB + 1) / 2;
+  extern __shared__ __align__(128) unsigned char s_raw[];
+  K* s_in = reinterpret_cast<K*>(s_raw);
+  uint32_t* s_inv = reinterpret_cast<uint32_t*>(s_raw + LY::SK);
+  K* s_out = reinterpret_cast<K*>(s_raw + LY::SK + LY::SV);
+  uint32_t* s_outv = reinterpret_cast<uint32_t*>(s_raw + LY::SK + LY::SV + LY::OK);
+  uint16_t* s_pref = reinterpret_cast<uint16_t*>(s_raw + LY::SK + LY::SV + LY::OK + LY::OV);
+  __shared__ uint32_t s_wsum[NW][NWORD];
+  __shared__ uint32_t s_blk[NWORD];
+  __shared__ uint32_t s_run[NB], s_tot[NB], s_dst[NB], s_pe[NB];
+  __shared__ __align__(8) uint64_t s_bar;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+  const uint32_t total = tb.blk_prefix[nseg];
+  const uint32_t G = gridDim.x;
+  uint32_t b = blockIdx.x;
+  if (b >= total) return;
+  if (tid == 0) mbar_init(&s_bar, 1);
+  mbar_fence_init();
+  __syncthreads();
+
+  auto geom = [&](uint32_t bb, uint32_t& sg, uint64_t& beg, uint32_t& cnt) {
+    sg = find_seg(tb.blk_prefix, nseg, bb);
+    beg = tb.seg_off[sg] + static_cast<uint64_t>(bb - tb.blk_prefix[sg]) * part_tile;
+    cnt = static_cast<uint32_t>(min64(part_tile, tb.seg_off[sg + 1] - beg));
+  };
+  auto issue = [&](uint32_t bb) {  // warp 0
+    uint32_t sg, c;
+    uint64_t bg;
+    geom(bb, sg, bg, c);
+    if (lane == 0) fence_proxy_async();  // the generic reads of the stage happened before the last barrier
+    __syncwarp();
+    const PendingBulk<K> pk = load_window_singles(s_in, phase_of(keys_in + bg), keys_in + bg, c, lane);
+    PendingBulk<uint32_t> pv{nullptr, nullptr, 0};
+    if constexpr (HAS_V) pv = load_window_singles(s_inv, phase_of(vals_in + bg), vals_in + bg, c, lane);
+    cp_async_mbar_arrive(&s_bar);
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&s_bar, pk.bytes + pv.bytes);
+      if (pk.bytes) bulk_g2s(pk.sdst, pk.gsrc, pk.bytes, &s_bar);
+      if (HAS_V && pv.bytes) bulk_g2s(pv.sdst, pv.gsrc, pv.bytes, &s_bar);
+    }
+  };
+  // absolute first position and packet end of every packet of block bb (threads < NB)
+  auto load_dst = [&](uint32_t bb, uint32_t& d, uint32_t& e) {
+    const uint32_t sg = find_seg(tb.blk_prefix, nseg, bb);
+    const uint32_t first = tb.blk_prefix[sg], nb_s = tb.blk_prefix[sg + 1] - first;
+    d = tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(tid) * nb_s + (bb - first)];
+    e = static_cast<uint32_t>(tb.pkt_off[static_cast<size_t>(sg) * NB + tid + 1]);
+  };
+
+  if (wid == 0) issue(b);
+  uint32_t nd = 0, npe = 0;
+  if (tid < NB) load_dst(b, nd, npe);
+  uint32_t parity = 0;
+  bool failed = false;
+  for (; b < total; b += G) {
+    uint32_t seg, cnt;
+    uint64_t beg;
+    geom(b, seg, beg, cnt);
+    if (tid < NB) {
+      s_dst[tid] = nd;
+      s_pe[tid] = npe;
+      if (b + G < total) load_dst(b + G, nd, npe);
+    }
+    const bool ok = mbar_wait_bounded(&s_bar, parity, tb.err, kWaitNs);
+    parity ^= 1;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const bool flip = tb.seg_flip[seg] != 0;
+    const DigitRule rule = (NB == 10) ? rule_dec(static_cast<int>(tb.seg_class[seg]))
+                                      : make_rule_bin(static_cast<int>(tb.seg_class[seg]));
+    const K* rk = s_in + phase_of(keys_in + beg);
+    const uint32_t* rv = HAS_V ? s_inv + phase_of(vals_in + beg) : nullptr;
+    K k[IPT];
+    uint32_t v[IPT];
+    uint32_t pr[IPT];  // packet in bits 0..7 (NB = none), local rank from bit 8
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t i = tid * IPT + j;
+      if (i < cnt) {
+        k[j] = rk[i];
+        if constexpr (HAS_V) v[j] = rv[i];
+        const uint32_t p = packet_of<NB>(KT<K>::image(k[j], flip), rule);
+        const uint32_t sh = 4 * (p & 7);
+        const uint32_t lr = (((p < 8) ? lo : hi) >> sh) & 15u;
+        if (p < 8) lo += 1u << sh; else hi += 1u << sh;
+        pr[j] = p | (lr << 8);
+      } else {
+        pr[j] = NB;
+      }
+    }
+    __syncthreads();  // every item is in registers: the stage may be refilled
+    if (wid == 0 && b + G < total) issue(b + G);
+    // local counts, two packets per word, and their block-wide scan
+    uint32_t wv[NWORD], incl[NWORD];
+#pragma unroll
+    for (int q = 0; q < NWORD; ++q) {
+      const uint32_t c0 = (((2 * q < 8) ? lo : hi) >> (4 * ((2 * q) & 7))) & 15u;
+      const uint32_t c1 = (2 * q + 1 < NB) ? ((((2 * q + 1 < 8) ? lo : hi) >> (4 * ((2 * q + 1) & 7))) & 15u) : 0u;
+      wv[q] = c0 | (c1 << 16);
+      uint32_t x = wv[q];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      incl[q] = x;
+      if (lane == 31) s_wsum[wid][q] = x;
+    }
+    if (wid == 0 && lane == 0) bulk_wait_read0();  // the previous block's stores have read the staging buffer
+    __syncthreads();
+    if (wid == 0) {
+      if (lane < NWORD) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const uint32_t t = s_wsum[w][lane];
+          s_wsum[w][lane] = run;
+          run += t;
+        }
+        s_blk[lane] = run;
+      }
+      __syncwarp();
+      // staging start of every run: at its destination's 16-byte phase
+      uint32_t tot = 0, units = 0;
+      if (lane < NB) {
+        tot = (s_blk[lane >> 1] >> (16 * (lane & 1))) & 0xffffu;
+        units = (tot + 3) / 4 + 1;
+      }
+      uint32_t x = units;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane < NB) {
+        s_run[lane] = 4 * (x - units) + (s_dst[lane] & 3u);
+        s_tot[lane] = tot;
+      }
+    }
+    __syncthreads();
+    // this thread's first staging position in every packet
+#pragma unroll
+    for (int p = 0; p < NB; ++p) {
+      const uint32_t ex = incl[p >> 1] - wv[p >> 1] + s_wsum[wid][p >> 1];
+      s_pref[tid * NB + p] = static_cast<uint16_t>(s_run[p] + ((ex >> (16 * (p & 1))) & 0xffffu));
+    }
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t p = pr[j] & 0xffu;
+      if (p < NB) {
+        const uint32_t pos = s_pref[tid * NB + p] + (pr[j] >> 8);
+        s_out[pos] = k[j];
+        if constexpr (HAS_V) s_outv[pos] = v[j];
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll 1
+      for (int p = 0; p < NB; ++p) {
+        const uint32_t t = s_tot[p];
+        if (t == 0) continue;
+        const uint32_t d = s_dst[p];
+        if (d + t > s_pe[p]) {
+          if (lane == 0) atomicOr(tb.err, kErrBounds);
+          continue;
+        }
+        store_window(keys_out + d, s_out + s_run[p], t, lane);
+        if constexpr (HAS_V) store_window(vals_out + d, s_outv + s_run[p], t, lane);
+      }
+      if (lane == 0) bulk_commit();
+    }
+  }
+  // the copy that did not arrive may still be in flight into the stage: give
+  // it a bounded chance to land before the CTA's shared memory is released
+  if (failed) mbar_wait_bounded(&s_bar, parity ^ 1u, tb.err, kWaitNs);
+  if (tid == 0) bulk_wait0();
+}
+
 }  // namespace hs

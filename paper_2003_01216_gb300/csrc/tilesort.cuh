@@ -76,9 +76,11 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
     if constexpr (HAS_V) transposition_sort<IPT>(k, v);
     else network_sort<IPT>(k);
 
-    // merge levels: runs of `run` items -> 2 * run, in the region at offset 0
+    // merge levels: runs of `run` = IPT << lv items -> 2 * run, in the region
+    // at offset 0; a pair of runs is merged by 2 << lv threads, IPT outputs each
 #pragma unroll 1
-    for (int run = IPT; run < TILE; run <<= 1) {
+    for (int lv = 0; (IPT << lv) < TILE; ++lv) {
+      const int run = IPT << lv;
       __syncthreads();
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
@@ -86,11 +88,11 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
         if constexpr (HAS_V) rv[tid * IPT + j] = v[j];
       }
       __syncthreads();
-      const int tpg = (2 * run) / IPT;
-      const int a0 = (tid / tpg) * 2 * run;
-      const int diag = (tid % tpg) * IPT;
+      const int g = tid >> (lv + 1);                    // pair of runs
+      const int diag = (tid & ((2 << lv) - 1)) * IPT;   // first output inside the pair
+      const int a0 = g * 2 * run;
       const K* sA = rk + a0;
-      const K* sB = rk + a0 + run;
+      const K* sB = sA + run;
       const int i = corank_smem(sA, run, sB, run, diag);
       int src[IPT];
       serial_merge<K, IPT, true, HAS_V>(sA, i, run, sB, diag - i, run, IPT, k, src);

@@ -92,6 +92,9 @@ def test_caller_workspace(oracle):
     assert_equal(tk.cpu().numpy(), oracle.sort(keys)[0], "sort in a caller work space")
     with pytest.raises(hs.HsError):
         hs.sort_keys(tk, workspace=ws[: need // 2])
+    big = torch.empty(need + 512, dtype=torch.uint8, device=dev())
+    with pytest.raises(hs.HsError):  # the work space must be 256-byte aligned
+        hs.sort_keys(tk, workspace=big[16:16 + need])
 
 
 def test_host_buffers(oracle):
