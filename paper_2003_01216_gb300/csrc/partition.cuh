@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
     beg = tb.seg_off[sg] + static_cast<uint64_t>(bb - tb.blk_prefix[sg]) * part_tile;
     cnt = static_cast<uint32_t>(min64(part_tile, tb.seg_off[sg + 1] - beg));
   };
-  auto issue = [&](uint32_t bb) {  // warp 0
+  auto issue = [&](uint32_t bb) {  // one warp (the last)
     uint32_t sg, c;
     uint64_t bg;
     geom(bb, sg, bg, c);
@@ -626,7 +626,8 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
     e = static_cast<uint32_t>(tb.pkt_off[static_cast<size_t>(sg) * NB + tid + 1]);
   };
 
-  if (wid == 0) issue(b);
+  constexpr int kIssueWarp = NW - 1;  // warp 0 computes the run offsets
+  if (wid == kIssueWarp) issue(b);
   uint32_t nd = 0, npe = 0;
   if (tid < NB) load_dst(b, nd, npe);
   uint32_t parity = 0;
@@ -655,23 +656,28 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
     uint32_t v[IPT];
     uint32_t pr[IPT];  // packet in bits 0..7 (NB = none), local rank from bit 8
     uint32_t lo = 0, hi = 0;
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
+    auto take = [&](int j) {
       const uint32_t i = tid * IPT + j;
-      if (i < cnt) {
-        k[j] = rk[i];
-        if constexpr (HAS_V) v[j] = rv[i];
-        const uint32_t p = packet_of<NB>(KT<K>::image(k[j], flip), rule);
-        const uint32_t sh = 4 * (p & 7);
-        const uint32_t lr = (((p < 8) ? lo : hi) >> sh) & 15u;
-        if (p < 8) lo += 1u << sh; else hi += 1u << sh;
-        pr[j] = p | (lr << 8);
-      } else {
-        pr[j] = NB;
+      k[j] = rk[i];
+      if constexpr (HAS_V) v[j] = rv[i];
+      const uint32_t p = packet_of<NB>(KT<K>::image(k[j], flip), rule);
+      const uint32_t sh = 4 * (p & 7);
+      const uint32_t lr = (((p < 8) ? lo : hi) >> sh) & 15u;
+      if (p < 8) lo += 1u << sh; else hi += 1u << sh;
+      pr[j] = p | (lr << 8);
+    };
+    if (cnt == static_cast<uint32_t>(LY::TILE)) {  // full block: no bounds tests
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) take(j);
+    } else {
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        if (tid * IPT + j < cnt) take(j);
+        else pr[j] = NB;
       }
     }
     __syncthreads();  // every item is in registers: the stage may be refilled
-    if (wid == 0 && b + G < total) issue(b + G);
+    if (wid == kIssueWarp && b + G < total) issue(b + G);
     // local counts, two packets per word, and their block-wide scan
     uint32_t wv[NWORD], incl[NWORD];
 #pragma unroll
@@ -688,7 +694,7 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
       incl[q] = x;
       if (lane == 31) s_wsum[wid][q] = x;
     }
-    if (wid == 0 && lane == 0) bulk_wait_read0();  // the previous block's stores have read the staging buffer
+    if (lane == 0) bulk_wait_read0();  // this warp's stores of the previous block have read the staging buffer
     __syncthreads();
     if (wid == 0) {
       if (lane < NWORD) {
@@ -737,26 +743,27 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
     }
     fence_proxy_async();
     __syncthreads();
-    if (wid == 0) {
+    // warp w stores the runs of packets w, w + NW, ...
+    bool stored = false;
 #pragma unroll 1
-      for (int p = 0; p < NB; ++p) {
-        const uint32_t t = s_tot[p];
-        if (t == 0) continue;
-        const uint32_t d = s_dst[p];
-        if (d + t > s_pe[p]) {
-          if (lane == 0) atomicOr(tb.err, kErrBounds);
-          continue;
-        }
-        store_window(keys_out + d, s_out + s_run[p], t, lane);
-        if constexpr (HAS_V) store_window(vals_out + d, s_outv + s_run[p], t, lane);
+    for (int p = wid; p < NB; p += NW) {
+      const uint32_t t = s_tot[p];
+      if (t == 0) continue;
+      const uint32_t d = s_dst[p];
+      if (d + t > s_pe[p]) {
+        if (lane == 0) atomicOr(tb.err, kErrBounds);
+        continue;
       }
-      if (lane == 0) bulk_commit();
+      store_window(keys_out + d, s_out + s_run[p], t, lane);
+      if constexpr (HAS_V) store_window(vals_out + d, s_outv + s_run[p], t, lane);
+      stored = true;
     }
+    if (stored && lane == 0) bulk_commit();
   }
   // the copy that did not arrive may still be in flight into the stage: give
   // it a bounded chance to land before the CTA's shared memory is released
   if (failed) mbar_wait_bounded(&s_bar, parity ^ 1u, tb.err, kWaitNs);
-  if (tid == 0) bulk_wait0();
+  if (lane == 0) bulk_wait0();
 }
 
 }  // namespace hs
