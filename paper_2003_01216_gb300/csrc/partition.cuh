@@ -133,29 +133,24 @@ __device__ __forceinline__ void hist_count_block(const K* keysrc, bool from_smem
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (int q = tid; q < NB; q += BLOCK) s_cnt[q] = 0;
   U u[IPT];
-  bool any_neg = false;
   U m = 0;
+  const bool full = cnt == static_cast<uint32_t>(BLOCK * IPT);
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
     const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
-    if (i < cnt) {
-      const K k = keysrc[i];
-      any_neg |= KT<K>::negative(k);
-      u[j] = KT<K>::image(k, flip);
-      m = max(m, u[j]);
-    } else {
-      u[j] = 0;
-    }
+    u[j] = (full || i < cnt) ? KT<K>::image(keysrc[i], flip) : U(0);
+    m = max(m, u[j]);
   }
   (void)from_smem;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, static_cast<U>(__shfl_xor_sync(0xffffffffu, m, o)));
   if (lane == 0) s_max[wid] = m;
-  if (img == 0 && __any_sync(0xffffffffu, any_neg) && lane == 0) s_neg = 1;
   __syncthreads();
   m = s_max[0];
 #pragma unroll
   for (int w = 1; w < NW; ++w) m = max(m, s_max[w]);
+  // int32 under the identity image: a negative key is an image with the top bit set
+  if (std::is_same<K, int32_t>::value && img == 0 && tid == 0 && (static_cast<uint64_t>(m) >> 31)) s_neg = 1;
   const int cls = (NB == 10) ? dec_class(m) : bin_class(m);
   const DigitRule rule = (NB == 10) ? rule_dec(cls) : make_rule_bin(cls);
   if constexpr (NB == 10) {
@@ -167,7 +162,7 @@ __device__ __forceinline__ void hist_count_block(const K* keysrc, bool from_smem
     for (int j = 0; j < IPT; ++j) {
       const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
       const uint32_t p = packet_of<NB>(u[j], rule);
-      const uint32_t inc = (i < cnt) ? (1u << (4 * (p & 7))) : 0u;
+      const uint32_t inc = (full || i < cnt) ? (1u << (4 * (p & 7))) : 0u;
       if (p < 8) lo += inc; else hi += inc;
     }
 #pragma unroll
@@ -180,7 +175,7 @@ __device__ __forceinline__ void hist_count_block(const K* keysrc, bool from_smem
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
-      const uint32_t q = (i < cnt) ? packet_of<NB>(u[j], rule) : NB;
+      const uint32_t q = (full || i < cnt) ? packet_of<NB>(u[j], rule) : NB;
       const uint32_t peers = __match_any_sync(0xffffffffu, q);
       if (q < NB && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[q], __popc(peers));
     }
@@ -237,7 +232,7 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
     cnt = static_cast<uint32_t>(min64(part_tile, tb.seg_off[sg + 1] - beg));
   };
   constexpr size_t STAGE = ((region_elems(TILE) * sizeof(K) + 127) & ~size_t(127));
-  auto issue = [&](uint32_t bb, int st) {  // warp 0
+  auto issue = [&](uint32_t bb, int st) {  // the last warp (warp 0 leads the block reductions)
     uint64_t beg;
     uint32_t cnt;
     block_span(bb, seg, beg, cnt);
@@ -253,7 +248,7 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
     }
   };
 
-  if (img == 0 && wid == 0) issue(b0, 0);
+  if (img == 0 && wid == NW - 1) issue(b0, 0);
   uint32_t par0 = 0, par1 = 0;
   int st = 0;
   for (uint32_t b = b0; b < b1; ++b) {
@@ -265,7 +260,7 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
     const uint32_t cnt = static_cast<uint32_t>(min64(part_tile, tb.seg_off[seg + 1] - beg));
     int cls = 0;
     if (img == 0) {
-      if (wid == 0 && b + 1 < b1) issue(b + 1, st ^ 1);
+      if (wid == NW - 1 && b + 1 < b1) issue(b + 1, st ^ 1);
       const bool ok = mbar_wait_bounded(&s_bar[st], st ? par1 : par0, tb.err, 2000000000ull);
       if (st) par1 ^= 1; else par0 ^= 1;
       if (__syncthreads_or(!ok)) {
