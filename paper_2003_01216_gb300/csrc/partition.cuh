@@ -421,7 +421,7 @@ static __global__ void k_scan_units(uint32_t m, Tables tb) {
 // checked against its packet's end (kErrBounds on violation, write skipped).
 // ---------------------------------------------------------------------------
 template <class K, bool HAS_V, int NB, int BLOCK, int IPT>
-__global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+__global__ void __launch_bounds__(BLOCK, 2) k_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                                                     K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                     uint32_t nseg, uint32_t part_tile, Tables tb) {
   constexpr int NW = BLOCK / kWarp;
@@ -470,13 +470,17 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
       rq[j] = NB;
     }
   }
-  // warp ranking in input order
+  // warp ranking in input order; every item's peers first (independent
+  // matches overlap), then the running per-warp counts
   uint32_t* wc = s_wc + wid * NBX;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t pm[IPT];
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) pm[j] = __match_any_sync(0xffffffffu, rq[j]);
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
     const uint32_t q = rq[j];
-    const uint32_t peers = __match_any_sync(0xffffffffu, q);
+    const uint32_t peers = pm[j];
     const uint32_t base = wc[q];
     rq[j] = q | ((base + __popc(peers & lt_mask)) << 16);
     __syncwarp();
@@ -496,14 +500,13 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
     s_bs[p] = run;
   }
   __syncthreads();
-  if (tid == 0) {  // block packet starts: exclusive scan of the totals
-    uint32_t run = 0;
-    for (int p = 0; p < NB; ++p) {
-      const uint32_t c = s_bs[p];
-      s_bs[p] = run;
-      run += c;
-    }
-    s_bs[NB] = run;
+  {  // block packet starts: exclusive scan of the totals (one packet per thread)
+    static_assert(NB <= BLOCK && BLOCK == kScanBlock, "one packet per thread");
+    __shared__ uint32_t s_warp[32];
+    const uint32_t c = (tid < NB) ? s_bs[tid] : 0u;
+    const uint32_t incl = block_incl_scan(c, s_warp);
+    if (tid < NB) s_bs[tid] = incl - c;
+    if (tid == NB - 1) s_bs[NB] = incl;
   }
   __syncthreads();
   // staged element e of packet p goes to e + (first position - block start) of p
