@@ -69,9 +69,11 @@ typedef struct {
   int tile;             /* keys per tile of the per-packet sort; 0 = the built tile for the call
                            (7936 for 4-byte keys without values, else 3840; see hs_plan_describe).
                            Any other value returns HS_ERR_UNSUPPORTED */
-  int fan_in;           /* runs merged per merge pass (Fig. 1(b) merges two): 2 (default, also 0)
-                           or 4 (every pass merges groups of four adjacent runs, so half the
-                           passes over memory; same result bit for bit).  Other values
+  int fan_in;           /* runs merged per merge pass (Fig. 1(b) merges two): 2, or 4 (every
+                           pass merges groups of four adjacent runs, so half the passes over
+                           memory; same result bit for bit), or 0 = tuned: the entry of the
+                           tuning table (hs_tune_set) for this key type, values, partition
+                           and size bucket, else 4 up to 2^24 keys and 2 above.  Other values
                            return HS_ERR_UNSUPPORTED */
   int stop_after;       /* testing: 0 = whole sort; 1 = stop after the packet step
                            (array holds the stable packet layout); 2 = stop after the
@@ -200,6 +202,17 @@ hs_status hs_timing_read(hs_kernel_time* out, int max, int* count);
 
 /* Destroy every cached CUDA graph (see hs_opts.graph). */
 hs_status hs_graph_cache_clear(void);
+
+/* Tuning table (process-wide, thread-safe): the merge fan-in that calls with
+ * opts->fan_in == 0 use, per (key type, has values, partition, size bucket);
+ * bucket = ceil(log2(n)) (0..32).  Filled by a tuner that times the candidates
+ * on this GPU (the Python package's tune module) or by the caller.
+ * hs_tune_set: fan_in 2 or 4 (else HS_ERR_INVALID); partition 1, 10 or 256.
+ * hs_tune_get: the fan-in a call with fan_in == 0 would use for n keys
+ * (table entry, else the built-in rule).  hs_tune_clear: empties the table. */
+hs_status hs_tune_set(hs_dtype dtype, int has_vals, int partition, int log2n, int fan_in);
+hs_status hs_tune_get(hs_dtype dtype, int has_vals, int partition, size_t n, int* fan_in);
+hs_status hs_tune_clear(void);
 
 /* Cumulative number of kernel launches this library has enqueued in this
  * process (memsets and copies not counted; a graph replay counts the kernels

@@ -20,7 +20,7 @@ EXPORTS = [
     "hs_sort_keys", "hs_sort_pairs", "hs_sort_batch", "hs_sort_keys_host", "hs_workspace_size",
     "hs_workspace_reserve", "hs_workspace_release", "hs_stream_error", "hs_plan_describe",
     "hs_timing_enable", "hs_timing_read", "hs_kernel_launches", "hs_status_string", "hs_last_error",
-    "hs_sort_keys_noalloc", "hs_graph_cache_clear",
+    "hs_sort_keys_noalloc", "hs_graph_cache_clear", "hs_tune_set", "hs_tune_get", "hs_tune_clear",
 ]
 
 
@@ -80,6 +80,9 @@ def lib() -> ctypes.CDLL:
         L.hs_workspace_reserve.argtypes = [sz, p]
         L.hs_workspace_release.argtypes = []
         L.hs_graph_cache_clear.argtypes = []
+        L.hs_tune_set.argtypes = [i, i, i, i, i]
+        L.hs_tune_get.argtypes = [i, i, i, sz, p]
+        L.hs_tune_clear.argtypes = []
         L.hs_stream_error.argtypes = [p]
         L.hs_plan_describe.argtypes = [i, sz, i, sz, p, p]
         L.hs_timing_enable.argtypes = [i]

@@ -123,14 +123,39 @@ hs_status grow(std::map<std::pair<int, cudaStream_t>, Buf>& m, cudaStream_t st, 
 
 size_t key_bytes(hs_dtype dt) { return dt == HS_UINT64 ? 8 : 4; }
 
+// Tuning table: merge fan-in per (key type, values, partition, size bucket).
+struct TuneKey {
+  int dtype, has_vals, partition, log2n;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dtype, has_vals, partition, log2n) < std::tie(o.dtype, o.has_vals, o.partition, o.log2n);
+  }
+};
+std::map<TuneKey, int> g_tune;
+std::mutex g_tune_mu;
+
+int size_bucket(size_t n) {
+  int b = 0;
+  while (b < 63 && (static_cast<size_t>(1) << b) < n) ++b;
+  return b;
+}
+int tuned_fan_in(int dtype, bool has_vals, int partition, size_t n) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(TuneKey{dtype, has_vals ? 1 : 0, partition, size_bucket(n)});
+    if (it != g_tune.end()) return it->second;
+  }
+  // built-in rule from one GB300: four-way passes win while passes are short
+  // (launch- and latency-bound), two-way passes above 2^24 keys
+  return n <= (static_cast<size_t>(1) << 24) ? 4 : 2;
+}
+
 hs_status check_opts(const hs_opts* opts, hs_opts* o) {
   hs_opts d{};
   if (opts) d = *opts;
   if (d.partition == 0) d.partition = 10;
   if (d.partition != 1 && d.partition != 10 && d.partition != 256) return HS_ERR_INVALID;
   if (d.tile != 0 && d.tile != kBlock * 15 && d.tile != kBlock * 31) return HS_ERR_UNSUPPORTED;
-  if (d.fan_in == 0) d.fan_in = 2;
-  if (d.fan_in != 2 && d.fan_in != 4) return HS_ERR_UNSUPPORTED;
+  if (d.fan_in != 0 && d.fan_in != 2 && d.fan_in != 4) return HS_ERR_UNSUPPORTED;
   if (d.stop_after < 0 || d.stop_after > 2) return HS_ERR_INVALID;
   *o = d;
   return HS_OK;
@@ -143,6 +168,7 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
   HS_TRY(check_opts(opts, &o));
   if (n >= (1ull << 32) || nseg >= (1ull << 24)) return HS_ERR_INVALID;
   if (n > 0 && !keys) return HS_ERR_INVALID;
+  if (o.fan_in == 0) o.fan_in = tuned_fan_in(static_cast<int>(dt), vals != nullptr, o.partition, n);
   if (o.tile != 0 && o.tile != sort_tile_for(key_bytes(dt), vals != nullptr)) return HS_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (n == 0 && !offs) {
@@ -332,6 +358,29 @@ hs_status hs_workspace_release(void) {
   return HS_OK;
 }
 
+hs_status hs_tune_set(hs_dtype dtype, int has_vals, int partition, int log2n, int fan_in) {
+  if (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64) return HS_ERR_INVALID;
+  if (partition != 1 && partition != 10 && partition != 256) return HS_ERR_INVALID;
+  if (log2n < 0 || log2n > 32 || (fan_in != 2 && fan_in != 4)) return HS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[TuneKey{static_cast<int>(dtype), has_vals ? 1 : 0, partition, log2n}] = fan_in;
+  return HS_OK;
+}
+
+hs_status hs_tune_get(hs_dtype dtype, int has_vals, int partition, size_t n, int* fan_in) {
+  if (!fan_in || (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64)) return HS_ERR_INVALID;
+  if (partition == 0) partition = 10;
+  if (partition != 1 && partition != 10 && partition != 256) return HS_ERR_INVALID;
+  *fan_in = tuned_fan_in(static_cast<int>(dtype), has_vals != 0, partition, n);
+  return HS_OK;
+}
+
+hs_status hs_tune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+  return HS_OK;
+}
+
 hs_status hs_graph_cache_clear(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto& kv : g_graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -371,6 +420,7 @@ hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, 
   (void)nseg;
   out->tile = sort_tile_for(key_bytes(dtype), has_vals != 0);
   out->part_tile = kTile;
+  if (o.fan_in == 0) o.fan_in = tuned_fan_in(static_cast<int>(dtype), has_vals != 0, o.partition, n);
   out->fan_in = o.fan_in;
   out->merge_passes = (n == 0) ? 0 : worst_passes(n, static_cast<size_t>(out->tile), o.fan_in);
   // seg_plan, hist (x2 for int32), finalize, fold, 3 scan kernels, pkt, scan_units, scatter,

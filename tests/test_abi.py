@@ -73,7 +73,7 @@ def test_plan_describe(n):
     for dtype, has_vals, tile in [(N.HS_INT32, False, 256 * 31), (N.HS_UINT32, False, 256 * 31),
                                   (N.HS_INT32, True, 256 * 15), (N.HS_UINT64, False, 256 * 15),
                                   (N.HS_UINT64, True, 256 * 15)]:
-        p = hs.plan(dtype, n, has_vals)
+        p = hs.plan(dtype, n, has_vals, fan_in=2)
         assert p["tile"] == tile and p["part_tile"] == 256 * 15
         tiles = -(-n // tile)
         passes = 0 if tiles <= 1 else math.ceil(math.log2(tiles))
@@ -82,7 +82,7 @@ def test_plan_describe(n):
         # kernels, packet offsets, tile prefix, scatter, tile sort, 2 per merge pass
         assert p["launches"] == (12 if dtype == N.HS_INT32 else 11) + 2 * passes
         # without the MSD step: seg_plan, packet table, tile prefix, tile sort
-        assert hs.plan(dtype, n, has_vals, partition=1)["launches"] == 4 + 2 * passes
+        assert hs.plan(dtype, n, has_vals, partition=1, fan_in=2)["launches"] == 4 + 2 * passes
         # fan-in 4: ceil(log4(tiles)) passes, still two launches each
         p4 = hs.plan(dtype, n, has_vals, fan_in=4)
         passes4 = 0 if tiles <= 1 else math.ceil(math.log(tiles, 4) - 1e-12)
@@ -97,3 +97,56 @@ def test_workspace_size_grows_with_n():
     b = hs.workspace_size(N.HS_INT32, 1 << 21)
     assert b > a >= 4 << 20
     assert hs.workspace_size(N.HS_UINT64, 1 << 20, has_vals=True) >= 12 << 20
+
+
+def test_tuning_table_and_default_rule():
+    import ctypes
+
+    import paper_2003_01216_gb300 as hs
+    from paper_2003_01216_gb300 import tune
+    lib = N.lib()
+    tune.clear()
+    try:
+        # built-in rule: four-way passes up to 2^24 keys, two-way above
+        assert tune.get(N.HS_INT32, 1 << 20) == 4 and tune.get(N.HS_INT32, (1 << 24) + 1) == 2
+        assert hs.plan(N.HS_INT32, 1 << 20)["fan_in"] == 4 and hs.plan(N.HS_INT32, 1 << 28)["fan_in"] == 2
+        # a table entry overrides the rule for its bucket only (bucket = ceil(log2 n))
+        tune.set_entry(N.HS_INT32, False, 10, 28, 4)
+        assert tune.get(N.HS_INT32, 1 << 28) == 4 and hs.plan(N.HS_INT32, 1 << 28)["fan_in"] == 4
+        assert tune.get(N.HS_INT32, (1 << 27) + 1) == 4 and tune.get(N.HS_INT32, (1 << 28) + 1) == 2
+        assert tune.get(N.HS_INT32, 1 << 28, has_vals=True) == 2 and tune.get(N.HS_UINT64, 1 << 28) == 2
+        assert tune.get(N.HS_INT32, 1 << 28, partition=256) == 2
+        # an explicit fan-in is never overridden
+        assert hs.plan(N.HS_INT32, 1 << 28, fan_in=2)["fan_in"] == 2
+        # invalid entries
+        assert lib.hs_tune_set(N.HS_INT32, 0, 10, 20, 3) == N.HS_ERR_INVALID
+        assert lib.hs_tune_set(N.HS_INT32, 0, 7, 20, 2) == N.HS_ERR_INVALID
+        assert lib.hs_tune_set(N.HS_INT32, 0, 10, 33, 2) == N.HS_ERR_INVALID
+        assert lib.hs_tune_set(5, 0, 10, 20, 2) == N.HS_ERR_INVALID
+        assert lib.hs_tune_get(N.HS_INT32, 0, 10, 5, None) == N.HS_ERR_INVALID
+        out = ctypes.c_int()
+        assert lib.hs_tune_get(N.HS_INT32, 0, 0, 1 << 20, ctypes.byref(out)) == N.HS_OK and out.value == 4
+        tune.clear()
+        assert tune.get(N.HS_INT32, 1 << 28) == 2
+    finally:
+        tune.clear()
+
+
+def test_tuning_cache_roundtrip(tmp_path):
+    from paper_2003_01216_gb300 import tune
+    tune.clear()
+    try:
+        entries = [{"dtype": "uint64", "has_vals": True, "partition": 10, "log2n": 22, "fan_in": 2,
+                    "ms": {"2": 1.0, "4": 1.5}},
+                   {"dtype": "int32", "has_vals": False, "partition": 256, "log2n": 30, "fan_in": 4,
+                    "ms": {"2": 9.0, "4": 8.0}}]
+        path = str(tmp_path / "tune.json")
+        tune.save(path, entries, device="GPU A")
+        assert tune.load(path, device="GPU B") == 0            # measured on another GPU: skipped
+        assert tune.get(N.HS_UINT64, 1 << 22, has_vals=True) == 4  # rule still in force
+        assert tune.load(path, device="GPU A") == 2
+        assert tune.get(N.HS_UINT64, 1 << 22, has_vals=True) == 2
+        assert tune.get(N.HS_INT32, 1 << 30, partition=256) == 4
+        assert tune.size_bucket(1) == 0 and tune.size_bucket(1 << 20) == 20 and tune.size_bucket((1 << 20) + 1) == 21
+    finally:
+        tune.clear()

@@ -157,3 +157,20 @@ def test_keys_graph_replay_counts_launches(oracle):
         assert_equal(work.cpu().numpy(), oracle.sort(keys)[0], f"graph sort seed {seed}")
     assert launches[0] == launches[1] == hs.plan(2, n)["launches"]
     hs.graph_cache_clear()
+
+
+def test_autotune_installs_a_correct_choice(oracle):
+    from paper_2003_01216_gb300 import tune
+    tune.clear()
+    try:
+        entries = tune.autotune(0, [1 << 16, 3 << 18], reps=2)
+        assert [e["log2n"] for e in entries] == [16, 20]
+        for e in entries:
+            assert set(e["ms"]) == {"2", "4"} and e["fan_in"] == min((2, 4), key=lambda f: e["ms"][str(f)])
+            assert tune.get(0, 1 << e["log2n"]) == e["fan_in"]
+        keys = I.generate("zipf", 3 << 18, seed=44)
+        gk, _, _, st = run(keys)  # fan_in = 0: the tuned entry
+        assert st == 0
+        assert_equal(gk, oracle.sort(keys)[0], "sort with the tuned fan-in")
+    finally:
+        tune.clear()
