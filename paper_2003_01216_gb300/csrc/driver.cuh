@@ -45,7 +45,7 @@ constexpr int kMerge4Spt = 2;  // fan-in-4 merge: chunk slots per tile (average 
 
 struct Layout {
   size_t keys_w, vals_w, seg_off, blk_prefix, cls_raw, cnt_raw, flat, scan_part, seg_neg, seg_cmax, seg_class,
-      seg_flip, pkt_off, unit_prefix, recs, list, any_neg, pass_ctl, total;
+      seg_flip, pkt_off, unit_prefix, recs, list, any_neg, pass_ctl, zero, zero_bytes, total;
   uint32_t max_blocks, max_units, npk;
 };
 
@@ -69,8 +69,13 @@ inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg
   L.cnt_raw = take(static_cast<size_t>(L.max_blocks) * nb * 4);
   L.flat = take(static_cast<size_t>(L.max_blocks) * nb * 4);
   L.scan_part = take(kScanChunks * 4);
-  L.seg_neg = take(nseg * 4);
-  L.seg_cmax = take(nseg * 2 * 4);
+  // seg_neg, seg_cmax, any_neg and pass_ctl are adjacent: one memset zeroes them
+  L.zero = take(nseg * 4 + nseg * 2 * 4 + 4 + kMaxPasses * 4);
+  L.seg_neg = L.zero;
+  L.seg_cmax = L.zero + nseg * 4;
+  L.any_neg = L.seg_cmax + nseg * 2 * 4;
+  L.pass_ctl = L.any_neg + 4;
+  L.zero_bytes = nseg * 4 + nseg * 2 * 4 + 4 + kMaxPasses * 4;
   L.seg_class = take(nseg * 4);
   L.seg_flip = take(nseg * 4);
   L.pkt_off = take((L.npk + 1) * 8);
@@ -78,8 +83,6 @@ inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg
   const size_t slots = static_cast<size_t>(L.max_units) * kMerge4Spt + 1;  // fan-in-4 chunk slots
   L.recs = take(std::max((static_cast<size_t>(L.max_units) + 1) * sizeof(MergeRec), slots * sizeof(Rec4)));
   L.list = take(slots * 4);
-  L.any_neg = take(4);
-  L.pass_ctl = take(kMaxPasses * 4);
   L.total = off;
   return L;
 }
@@ -178,11 +181,10 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
   const uint32_t nseg32 = static_cast<uint32_t>(nseg);
   Launcher lc(st);
 
-  // zero the per-segment flags and maxima
-  HS_TRY(lc.memset("zero_seg", tb.seg_neg, 0, nseg * 4));
-  HS_TRY(lc.memset("zero_cmax", tb.seg_cmax, 0, nseg * 2 * 4));
-  HS_TRY(lc.memset("zero_anyneg", tb.any_neg, 0, 4));
-  HS_TRY(lc.memset("zero_passctl", tb.pass_ctl, 0, kMaxPasses * 4));
+  // zero the per-segment flags and maxima and the pass control (one region)
+  HS_TRY(lc.memset("zero_tables", ws + L.zero, 0, L.zero_bytes));
+  const bool small = static_cast<uint64_t>(L.max_blocks) * NB <= kPlanSmallEntries &&
+                     static_cast<uint64_t>(L.npk) <= kPlanSmallEntries;
 
   lc.begin("seg_plan");
   k_seg_plan<<<1, 1024, 0, st>>>(offs, nseg32, n, kTile, tb);
@@ -191,12 +193,18 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
   if constexpr (NB == 1) {
     // no MSD step (ablation): every segment is one packet; the tile sort
     // reads the caller's array directly
-    lc.begin("pkt");
-    k_pkt_whole<<<(nseg32 + 255) / 256, 256, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
-    HS_TRY(lc.end());
-    lc.begin("scan_units");
-    k_scan_units<<<1, 1024, 0, st>>>(L.npk, tb);
-    HS_TRY(lc.end());
+    if (small) {
+      lc.begin("plan_small");
+      k_plan_small<1><<<1, 1024, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
+      HS_TRY(lc.end());
+    } else {
+      lc.begin("pkt");
+      k_pkt_whole<<<(nseg32 + 255) / 256, 256, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
+      HS_TRY(lc.end());
+      lc.begin("scan_units");
+      k_scan_units<<<1, 1024, 0, st>>>(L.npk, tb);
+      HS_TRY(lc.end());
+    }
   } else {
     {
       static int grid = 0;
@@ -209,6 +217,11 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
         HS_TRY(lc.end());
       }
     }
+    if (small) {
+      lc.begin("plan_small");
+      k_plan_small<NB><<<1, 1024, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
+      HS_TRY(lc.end());
+    } else {
     lc.begin("finalize");
     k_finalize<NB><<<(nseg32 + 255) / 256, 256, 0, st>>>(nseg32, tb);
     HS_TRY(lc.end());
@@ -240,6 +253,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     lc.begin("scan_units");
     k_scan_units<<<1, 1024, 0, st>>>(L.npk, tb);
     HS_TRY(lc.end());
+    }
 
     if constexpr (NB <= 16) {
       // persistent: bulk copies in and out, ranks from one scan of packed counts

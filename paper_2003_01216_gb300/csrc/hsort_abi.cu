@@ -417,15 +417,19 @@ hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, 
   if (!out || (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64)) return HS_ERR_INVALID;
   hs_opts o;
   HS_TRY(check_opts(opts, &o));
-  (void)nseg;
   out->tile = sort_tile_for(key_bytes(dtype), has_vals != 0);
   out->part_tile = kTile;
   if (o.fan_in == 0) o.fan_in = tuned_fan_in(static_cast<int>(dtype), has_vals != 0, o.partition, n);
   out->fan_in = o.fan_in;
   out->merge_passes = (n == 0) ? 0 : worst_passes(n, static_cast<size_t>(out->tile), o.fan_in);
   // seg_plan, hist (x2 for int32), finalize, fold, 3 scan kernels, pkt, scan_units, scatter,
-  // tilesort, 2 per merge pass; without the packet step: seg_plan, pkt, scan_units, tilesort
-  int l = (o.partition == 1) ? 3 : 1 + (dtype == HS_INT32 ? 2 : 1) + 1 + 1 + 3 + 1 + 1 + 1;
+  // tilesort, 2 per merge pass; without the packet step: seg_plan, pkt, scan_units, tilesort.
+  // Small calls run finalize .. scan_units (or pkt, scan_units) as one kernel.
+  const Layout L = make_layout(key_bytes(dtype), n, has_vals != 0, nseg ? nseg : 1, o.partition);
+  const bool small = static_cast<uint64_t>(L.max_blocks) * o.partition <= kPlanSmallEntries &&
+                     static_cast<uint64_t>(L.npk) <= kPlanSmallEntries;
+  const int plan_kernels = small ? 1 : (o.partition == 1 ? 2 : 7);
+  int l = (o.partition == 1) ? 1 + plan_kernels : 1 + (dtype == HS_INT32 ? 2 : 1) + plan_kernels + 1;
   if (o.stop_after != 1) l += 1;
   if (o.stop_after == 0) l += 2 * out->merge_passes;
   out->launches = (n == 0) ? 0 : l;

@@ -413,6 +413,131 @@ static __global__ void k_scan_units(uint32_t m, Tables tb) {
 }
 
 // ---------------------------------------------------------------------------
+// In-place exclusive scan of a[0, m) by the calling CTA alone (any multiple
+// of 32 threads up to 1024); the total goes to *total.  All threads call it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cta_exclusive_scan(uint32_t* a, uint32_t m, uint32_t* total, uint32_t* s_warp,
+                                                   uint32_t* s_carry) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) *s_carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < m; base += nt) {
+    const uint32_t i = base + tid;
+    const uint32_t x0 = (i < m) ? a[i] : 0u;
+    uint32_t v = x0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += x;
+    }
+    if (lane == 31) s_warp[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t w = (lane < (nt >> 5)) ? s_warp[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += x;
+      }
+      s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t incl = v + (wid ? s_warp[wid - 1] : 0u);
+    const uint32_t carry = *s_carry;
+    if (i < m) a[i] = carry + incl - x0;
+    __syncthreads();
+    if (tid == nt - 1) *s_carry = carry + incl;
+    __syncthreads();
+  }
+  if (tid == 0) *total = *s_carry;
+}
+
+// ---------------------------------------------------------------------------
+// k_plan_small: for small calls (at most kPlanSmallEntries block x packet and
+// segment x packet entries) the steps between the histogram and the scatter
+// -- k_finalize, k_fold, the three-kernel scan, k_pkt and k_scan_units -- in
+// one CTA, one launch instead of seven.  Same results, same tables.  With
+// NB == 1 (no MSD step) it is k_pkt_whole and k_scan_units.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPlanSmallEntries = 1u << 16;
+
+template <int NB>
+__global__ void __launch_bounds__(1024) k_plan_small(uint32_t nseg, uint32_t tile, Tables tb) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_carry;
+  const uint32_t tid = threadIdx.x, nt = blockDim.x;
+  const uint32_t m = nseg * NB;
+  if constexpr (NB == 1) {
+    for (uint32_t s = tid; s < nseg; s += nt) {
+      const uint64_t start = tb.seg_off[s], end = tb.seg_off[s + 1];
+      tb.pkt_off[s] = start;
+      const uint32_t tiles = static_cast<uint32_t>((end - start + tile - 1) / tile);
+      tb.unit_prefix[s] = tiles;
+      const uint32_t passes = static_cast<uint32_t>(passes_of(tiles, tb.fan_log2));
+      if (passes) atomicMax(&tb.pass_ctl[0], passes);
+    }
+    if (tid == 0) tb.pkt_off[nseg] = tb.seg_off[nseg];
+  } else {
+    // finalize: segment class and image
+    for (uint32_t s = tid; s < nseg; s += nt) {
+      const uint32_t neg = tb.seg_neg[s];
+      const bool empty = tb.blk_prefix[s + 1] == tb.blk_prefix[s];
+      const uint32_t C = tb.seg_cmax[s * 2 + (neg ? 1 : 0)];
+      tb.seg_class[s] = empty ? (NB == 10 ? 1u : 0u) : C;
+      tb.seg_flip[s] = neg;
+    }
+    __syncthreads();
+    // fold: every block's counts under its segment's class, (segment, packet, block) order
+    const uint32_t total = tb.blk_prefix[nseg];
+    for (uint32_t idx = tid; idx < total * NB; idx += nt) {
+      const uint32_t b = idx / NB, p = idx % NB;
+      const uint32_t s = find_seg(tb.blk_prefix, nseg, b);
+      const uint32_t first = tb.blk_prefix[s], nb_s = tb.blk_prefix[s + 1] - first;
+      const uint32_t C = tb.seg_class[s], cb = tb.cls_raw[b];
+      const uint32_t* raw = tb.cnt_raw + static_cast<size_t>(b) * NB;
+      uint32_t v = 0;
+      if constexpr (NB == 10) {
+        if (cb == C) {
+          v = raw[p];
+        } else if (p == 0) {  // every key of the block is below 10^(C-1): packet 0
+#pragma unroll
+          for (int t = 0; t < 10; ++t) v += raw[t];
+        }
+      } else {
+        const uint32_t d = (C > 8 ? C - 8 : 0) - (cb > 8 ? cb - 8 : 0);
+        const uint32_t lo = p << d, hi = min(static_cast<uint32_t>(NB), (p + 1) << d);
+        for (uint32_t t = lo; t < hi; ++t) v += raw[t];
+      }
+      tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s + (b - first)] = v;
+    }
+    __syncthreads();
+    // absolute first positions
+    uint32_t* grand = tb.scan_part;  // scratch word
+    cta_exclusive_scan(tb.flat, total * NB, grand, s_warp, &s_carry);
+    __syncthreads();
+    // packet starts and tiles
+    for (uint32_t idx = tid; idx < m; idx += nt) {
+      const uint32_t s = idx / NB, p = idx % NB;
+      const uint32_t first = tb.blk_prefix[s], nb_s = tb.blk_prefix[s + 1] - first;
+      const uint64_t start = nb_s ? tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s]
+                                  : tb.seg_off[s];
+      const uint64_t end = (nb_s && p + 1 < NB)
+                               ? tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p + 1) * nb_s]
+                               : tb.seg_off[s + 1];
+      tb.pkt_off[idx] = start;
+      const uint32_t tiles = static_cast<uint32_t>((end - start + tile - 1) / tile);
+      tb.unit_prefix[idx] = tiles;
+      const uint32_t passes = static_cast<uint32_t>(passes_of(tiles, tb.fan_log2));
+      if (passes) atomicMax(&tb.pass_ctl[0], passes);
+    }
+    if (tid == 0) tb.pkt_off[m] = tb.seg_off[nseg];
+  }
+  __syncthreads();
+  // first tile of every packet
+  cta_exclusive_scan(tb.unit_prefix, m, tb.unit_prefix + m, s_warp, &s_carry);
+}
+
+// ---------------------------------------------------------------------------
 // k_scatter: stable move into packets, one CTA per packet-step block.  Each
 // warp ranks its keys in input order (warp-striped items, a match over packet
 // ids); warps are ordered by position; the block's absolute first position
@@ -634,16 +759,18 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
     uint32_t seg, cnt;
     uint64_t beg;
     geom(b, seg, beg, cnt);
-    if (tid < NB) {
-      s_dst[tid] = nd;
-      s_pe[tid] = npe;
-      if (b + G < total) load_dst(b + G, nd, npe);
-    }
     const bool ok = mbar_wait_bounded(&s_bar, parity, tb.err, kWaitNs);
     parity ^= 1;
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
+    }
+    // after the barrier: every warp has finished the previous block's stores,
+    // which read s_dst and s_pe
+    if (tid < NB) {
+      s_dst[tid] = nd;
+      s_pe[tid] = npe;
+      if (b + G < total) load_dst(b + G, nd, npe);
     }
     const bool flip = tb.seg_flip[seg] != 0;
     const DigitRule rule = (NB == 10) ? rule_dec(static_cast<int>(tb.seg_class[seg]))

@@ -79,15 +79,20 @@ def test_plan_describe(n):
         passes = 0 if tiles <= 1 else math.ceil(math.log2(tiles))
         assert p["merge_passes"] == passes
         # seg_plan, histogram (+ flipped-image histogram for int32), finalize, fold, 3 scan
-        # kernels, packet offsets, tile prefix, scatter, tile sort, 2 per merge pass
-        assert p["launches"] == (12 if dtype == N.HS_INT32 else 11) + 2 * passes
+        # kernels, packet offsets, tile prefix, scatter, tile sort, 2 per merge pass; small
+        # calls (<= 2^16 block x packet entries) run finalize .. tile prefix as one kernel
+        blocks = -(-n // 3840) + 1
+        small = blocks * 10 <= 1 << 16
+        hist = 2 if dtype == N.HS_INT32 else 1
+        assert p["launches"] == 1 + hist + (1 if small else 7) + 2 + 2 * passes
         # without the MSD step: seg_plan, packet table, tile prefix, tile sort
-        assert hs.plan(dtype, n, has_vals, partition=1, fan_in=2)["launches"] == 4 + 2 * passes
+        small1 = blocks <= 1 << 16
+        assert hs.plan(dtype, n, has_vals, partition=1, fan_in=2)["launches"] == (3 if small1 else 4) + 2 * passes
         # fan-in 4: ceil(log4(tiles)) passes, still two launches each
         p4 = hs.plan(dtype, n, has_vals, fan_in=4)
         passes4 = 0 if tiles <= 1 else math.ceil(math.log(tiles, 4) - 1e-12)
         assert p4["fan_in"] == 4 and p4["merge_passes"] == passes4 == (passes + 1) // 2
-        assert p4["launches"] == (12 if dtype == N.HS_INT32 else 11) + 2 * passes4
+        assert p4["launches"] == 1 + hist + (1 if small else 7) + 2 + 2 * passes4
         assert p["fan_in"] == 2
 
 
