@@ -161,3 +161,29 @@ def test_special_values(oracle):
 def test_empty_input():
     gk, _, goff, st = run(np.zeros(0, np.int32))
     assert gk.size == 0 and st == 0 and np.all(goff == 0)
+
+
+@pytest.mark.parametrize("dist", ["reverse", "sorted", "equal", "distinct16", "uniform31", "int32full"])
+def test_persistent_ctas_loop_over_many_blocks(oracle, dist):
+    # 2^23 keys: every persistent CTA of the packet step and the tile sort
+    # handles many blocks in turn (the sizes above give each at most one), and
+    # sorted / reverse inputs make every block a single run of one packet
+    n = (1 << 23) + 1234
+    keys = I.generate(dist, n, seed=45)
+    vals = I.index_values(n)
+    lk, lv, loff = oracle.partition(keys, vals, 10)
+    for rep in range(2):
+        gk, gv, goff, st = run(keys, vals, 10, stop_after=1)
+        assert st == 0
+        assert_equal(goff, loff, f"{dist} packet offsets (pass {rep})")
+        assert_equal(gk, lk, f"{dist} packet layout (pass {rep})")
+        assert_equal(gv, lv, f"{dist} packet layout values (pass {rep})")
+    ek, ev, _ = oracle.sort(keys, vals, 10)
+    for fan in (2, 4):
+        gk, gv, _, st = run(keys, vals, 10, fan_in=fan)
+        assert st == 0
+        assert_equal(gk, ek, f"{dist} pair keys fan-in {fan}")
+        assert_equal(gv, ev, f"{dist} pair values fan-in {fan}")
+        gk, _, _, st = run(keys, None, 10, fan_in=fan)
+        assert st == 0
+        assert_equal(gk, ek, f"{dist} keys fan-in {fan}")
