@@ -100,7 +100,8 @@ typedef struct {
  * per-packet sort and bottom-up merge; the whole array is one "original
  * array" of the master node).
  *   dtype   HS_INT32 / HS_UINT32 / HS_UINT64 (4, 4, 8 bytes per key)
- *   d_keys  device pointer to n keys, any alignment of the element type
+ *   d_keys  device pointer to n keys, aligned to the key size (4 or 8 bytes;
+ *           else HS_ERR_INVALID), no other alignment needed
  *   n       element count; 0 is a no-op returning HS_OK
  * Returns HS_OK once the work is enqueued, HS_ERR_INVALID, HS_ERR_NOMEM or
  * HS_ERR_CUDA.
@@ -111,7 +112,8 @@ hs_status hs_sort_keys(hs_dtype dtype, void* d_keys, size_t n, const hs_opts* op
  * hs_sort_pairs -- sort n (key, value) pairs in place by key.  The order is
  * stable: equal keys keep their input order (merge sort's stability, Sec. 2.1;
  * ties broken by input index).  `stable` = 0 is accepted and returns the same
- * stable order.  d_vals: device pointer to n uint32 values, moved with their keys.
+ * stable order.  d_vals: device pointer to n uint32 values (4-byte aligned, else
+ * HS_ERR_INVALID), moved with their keys.
  */
 hs_status hs_sort_pairs(hs_dtype dtype, void* d_keys, uint32_t* d_vals, size_t n, int stable,
                         const hs_opts* opts, void* stream);
@@ -120,7 +122,8 @@ hs_status hs_sort_pairs(hs_dtype dtype, void* d_keys, uint32_t* d_vals, size_t n
  * hs_sort_batch -- segmented sort: nseg independent arrays stored back to
  * back in d_keys; segment s is [d_offsets[s], d_offsets[s+1]).  Each segment
  * goes through the whole method on its own (its own D and packets).
- *   d_offsets  device array of nseg + 1 uint64, non-decreasing, d_offsets[0] = 0,
+ *   d_offsets  device array of nseg + 1 uint64 (8-byte aligned, else HS_ERR_INVALID),
+ *              non-decreasing, d_offsets[0] = 0,
  *              d_offsets[nseg] = n (checked on the device: a violation sets
  *              the error word so hs_stream_error returns HS_ERR_INVALID, and no
  *              key moves)

@@ -168,6 +168,10 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
   HS_TRY(check_opts(opts, &o));
   if (n >= (1ull << 32) || nseg >= (1ull << 24)) return HS_ERR_INVALID;
   if (n > 0 && !keys) return HS_ERR_INVALID;
+  // element alignment (the kernels load whole elements)
+  if ((reinterpret_cast<uintptr_t>(keys) % key_bytes(dt)) || (reinterpret_cast<uintptr_t>(vals) & 3u) ||
+      (reinterpret_cast<uintptr_t>(offs) & 7u))
+    return HS_ERR_INVALID;
   if (o.fan_in == 0) o.fan_in = tuned_fan_in(static_cast<int>(dt), vals != nullptr, o.partition, n);
   if (o.tile != 0 && o.tile != sort_tile_for(key_bytes(dt), vals != nullptr)) return HS_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -303,7 +307,7 @@ hs_status hs_sort_batch(hs_dtype dtype, void* d_keys, uint32_t* d_vals, const ui
 hs_status hs_sort_keys_host(hs_dtype dtype, void* h_keys, size_t n, const hs_opts* opts, void* stream) {
   if (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64) return HS_ERR_INVALID;
   if (n == 0) return HS_OK;
-  if (!h_keys || n >= (1ull << 32)) return HS_ERR_INVALID;
+  if (!h_keys || n >= (1ull << 32) || (reinterpret_cast<uintptr_t>(h_keys) % key_bytes(dtype))) return HS_ERR_INVALID;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = n * key_bytes(dtype);
   char* d = nullptr;

@@ -63,6 +63,12 @@ def test_host_side_rejections():
     assert lib.hs_sort_batch(0, fake, None, fake, 0, 10, ctypes.byref(o), None) == N.HS_ERR_INVALID
     assert lib.hs_sort_keys(0, None, 0, ctypes.byref(o), None) == N.HS_OK                     # n = 0 no-op
     assert lib.hs_sort_keys_host(0, None, 5, None, None) == N.HS_ERR_INVALID
+    # element alignment: keys to their size, values to 4, offsets to 8 (checked before any CUDA call)
+    assert lib.hs_sort_keys(0, 0x1002, 10, ctypes.byref(o), None) == N.HS_ERR_INVALID
+    assert lib.hs_sort_keys(2, 0x1004, 10, ctypes.byref(o), None) == N.HS_ERR_INVALID
+    assert lib.hs_sort_pairs(0, 0x1000, 0x2002, 10, 1, ctypes.byref(o), None) == N.HS_ERR_INVALID
+    assert lib.hs_sort_batch(0, 0x1000, None, 0x3004, 2, 10, ctypes.byref(o), None) == N.HS_ERR_INVALID
+    assert lib.hs_sort_keys_host(2, 0x1004, 10, None, None) == N.HS_ERR_INVALID
 
 
 @pytest.mark.parametrize("n", [1, 3839, 3840, 3841, 7935, 7936, 7937, 1 << 20, 1 << 28])
