@@ -77,7 +77,11 @@ typedef struct {
                            return HS_ERR_UNSUPPORTED */
   int stop_after;       /* testing: 0 = whole sort; 1 = stop after the packet step
                            (array holds the stable packet layout); 2 = stop after the
-                           tile sort (every tile of every packet sorted on its own) */
+                           tile sort (every tile of every packet sorted on its own);
+                           2 + r (r = 1 .. 64) = stop after merge pass r (inside every
+                           packet, each group of fan_in^r tiles sorted on its own, pairs
+                           stably; packets needing fewer passes fully sorted).  Other
+                           values: HS_ERR_INVALID */
   uint64_t* d_packet_offsets_out; /* optional device array of partition*nseg + 1 uint64:
                            packet p of segment s spans [off[s*partition + p], off[s*partition+p+1])
                            as absolute element positions */

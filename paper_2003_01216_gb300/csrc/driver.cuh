@@ -310,7 +310,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       if (!cgrid) cgrid = persistent_grid(ck, 256, 0);
       Rec4* recs = reinterpret_cast<Rec4*>(ws + L.recs);
       uint32_t* list = reinterpret_cast<uint32_t*>(ws + L.list);
-      const int P = worst_passes(n, T, 4);
+      const int P = o.stop_after >= 3 ? std::min(worst_passes(n, T, 4), o.stop_after - 2) : worst_passes(n, T, 4);
       for (int r = 1; r <= P; ++r) {
         lc.begin("bound4");
         ck<<<cgrid, 256, 0, st>>>(keys, kw, recs, list, L.npk, r, tb);
@@ -327,7 +327,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       if (!mgrid) mgrid = persistent_grid(mk, kBlock, smem);
       if (!cgrid) cgrid = persistent_grid(ck, 256, 0);
       MergeRec* recs = reinterpret_cast<MergeRec*>(ws + L.recs);
-      const int P = worst_passes(n, sort_tile<K, HAS_V>());
+      const int P = o.stop_after >= 3 ? std::min(worst_passes(n, sort_tile<K, HAS_V>()), o.stop_after - 2)
+                                      : worst_passes(n, sort_tile<K, HAS_V>());
       for (int r = 1; r <= P; ++r) {
         lc.begin("corank");
         ck<<<cgrid, 256, 0, st>>>(keys, kw, recs, L.npk, r, tb);
@@ -336,6 +337,12 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
         mk<<<mgrid, kBlock, smem, st>>>(keys, vals, kw, vw, recs, r, tb);
         HS_TRY(lc.end());
       }
+    }
+    if (o.stop_after >= 3) {  // testing: the state after merge pass r, gathered into the caller's array
+      lc.begin("copy_back_pass");
+      k_copy_back_pass<K, HAS_V, sort_tile<K, HAS_V>()><<<2 * 152, 256, 0, st>>>(keys, vals, kw, vw, L.npk,
+                                                                                o.stop_after - 2, tb);
+      HS_TRY(lc.end());
     }
   }
   if (o.d_packet_offsets_out)

@@ -156,7 +156,7 @@ hs_status check_opts(const hs_opts* opts, hs_opts* o) {
   if (d.partition != 1 && d.partition != 10 && d.partition != 256) return HS_ERR_INVALID;
   if (d.tile != 0 && d.tile != kBlock * 15 && d.tile != kBlock * 31) return HS_ERR_UNSUPPORTED;
   if (d.fan_in != 0 && d.fan_in != 2 && d.fan_in != 4) return HS_ERR_UNSUPPORTED;
-  if (d.stop_after < 0 || d.stop_after > 2) return HS_ERR_INVALID;
+  if (d.stop_after < 0 || d.stop_after > 2 + kMaxPasses) return HS_ERR_INVALID;
   *o = d;
   return HS_OK;
 }
@@ -436,6 +436,7 @@ hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, 
   int l = (o.partition == 1) ? 1 + plan_kernels : 1 + (dtype == HS_INT32 ? 2 : 1) + plan_kernels + 1;
   if (o.stop_after != 1) l += 1;
   if (o.stop_after == 0) l += 2 * out->merge_passes;
+  if (o.stop_after >= 3) l += 2 * std::min(out->merge_passes, o.stop_after - 2) + 1;
   out->launches = (n == 0) ? 0 : l;
   return HS_OK;
 }

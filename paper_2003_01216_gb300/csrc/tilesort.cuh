@@ -129,4 +129,28 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
   if (tid == 0) bulk_wait0();
 }
 
+// ---------------------------------------------------------------------------
+// k_copy_back_pass (testing): after merge pass r every packet's data is in the
+// buffer that pass wrote -- W when the packet still needs passes after r and
+// (passes - r) is odd, else the caller's array U (a packet that needed fewer
+// passes finished in U).  Copies the W-resident tiles to U, one tile per CTA.
+// ---------------------------------------------------------------------------
+template <class K, bool HAS_V, int TILE>
+__global__ void k_copy_back_pass(K* ku, uint32_t* vu, const K* __restrict__ kw, const uint32_t* __restrict__ vw,
+                                 uint32_t npk, int r, Tables tb) {
+  const uint32_t total = tb.unit_prefix[npk];
+  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+    const uint32_t p = find_pkt(tb.unit_prefix, npk, u);
+    const uint32_t up0 = tb.unit_prefix[p], ntiles = tb.unit_prefix[p + 1] - up0;
+    const int passes = passes_of(ntiles, tb.fan_log2);
+    if (r > passes || ((passes - r) & 1) == 0) continue;  // this packet's data is in U
+    const uint64_t beg = tb.pkt_off[p] + static_cast<uint64_t>(u - up0) * TILE;
+    const uint32_t cnt = static_cast<uint32_t>(min64(TILE, tb.pkt_off[p + 1] - beg));
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      ku[beg + i] = kw[beg + i];
+      if constexpr (HAS_V) vu[beg + i] = vw[beg + i];
+    }
+  }
+}
+
 }  // namespace hs

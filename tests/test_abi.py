@@ -102,6 +102,18 @@ def test_plan_describe(n):
         assert p["fan_in"] == 2
 
 
+def test_stop_after_merge_pass_plan():
+    import paper_2003_01216_gb300 as hs
+    full = hs.plan(N.HS_INT32, 1 << 24, fan_in=2)
+    for r in (1, 3, full["merge_passes"], full["merge_passes"] + 5):
+        p = hs.plan(N.HS_INT32, 1 << 24, fan_in=2, stop_after=2 + r)
+        # the passes up to r, then one copy-back kernel
+        assert p["launches"] == full["launches"] - 2 * full["merge_passes"] + 2 * min(r, full["merge_passes"]) + 1
+    lib = N.lib()
+    assert lib.hs_sort_keys(0, ctypes.c_void_p(0x1000), 10, ctypes.byref(N.make_opts(stop_after=67)), None) == \
+        N.HS_ERR_INVALID
+
+
 def test_workspace_size_grows_with_n():
     import paper_2003_01216_gb300 as hs
     a = hs.workspace_size(N.HS_INT32, 1 << 20)

@@ -187,3 +187,29 @@ def test_persistent_ctas_loop_over_many_blocks(oracle, dist):
         gk, _, _, st = run(keys, None, 10, fan_in=fan)
         assert st == 0
         assert_equal(gk, ek, f"{dist} keys fan-in {fan}")
+
+
+@pytest.mark.parametrize("fan", [2, 4])
+@pytest.mark.parametrize("nb", [1, 10])
+@pytest.mark.parametrize("dist", ["uniform1e9", "zipf", "uniform64", "distinct2p24"])
+def test_merge_passes_one_by_one(oracle, dist, nb, fan):
+    # the state after every merge pass r: inside each packet every group of
+    # fan^r tiles is sorted on its own (pairs stably), the rest untouched by
+    # later passes -- the oracle's tile sort with tile * fan^r
+    n = 40 * TILE + 123
+    keys = I.generate(dist, n, seed=46)
+    vals = I.index_values(n)
+    lk, lv, off = oracle.partition(keys, vals, nb)
+    for has_vals in (False, True):
+        tile = tile_of(keys, has_vals)
+        code = hs.dtype_code(__import__("torch").from_numpy(keys[:1]))
+        passes = hs.plan(code, n, has_vals, partition=nb, fan_in=fan)["merge_passes"]
+        assert passes >= 2
+        for r in range(1, passes + 1):
+            ek, ev = oracle.tile_sort(lk, off, tile * fan ** r, lv if has_vals else None)
+            gk, gv, goff, st = run(keys, vals if has_vals else None, nb, stop_after=2 + r, fan_in=fan)
+            assert st == 0
+            assert_equal(goff, off, f"{dist} packet offsets after pass {r}")
+            assert_equal(gk, ek, f"{dist} keys after merge pass {r} (fan-in {fan}, values {has_vals})")
+            if has_vals:
+                assert_equal(gv, ev, f"{dist} values after merge pass {r} (fan-in {fan})")
