@@ -314,9 +314,9 @@ def main():
     mk = "merge4" if plan["fan_in"] == 4 else "merge"
 
     # timed region: K steps, each bracketed by events on the launching stream
+    # (no per-kernel instrumentation here: the split below comes from a
+    # separate instrumented run of the same steps)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    hs.timing_enable(True)
-    hs.timing_read()  # clear
     with ClockSampler(local) as clk:
         barrier(world, dev)
         torch.cuda.synchronize()
@@ -331,11 +331,21 @@ def main():
         barrier(world, dev)
         region_s = time.perf_counter() - t_region
         launches = hs.kernel_launches() - l0
-    per_kernel = hs.timing_read()
-    hs.timing_enable(False)
     err = hs.stream_error()
     if err != 0:
         raise RuntimeError(f"device error {err} during the timed region")
+    # per-kernel split: the same steps again with the library's event pair
+    # around every launch (which also turns programmatic launches off)
+    split_steps = min(args.steps, 5)
+    hs.timing_enable(True)
+    hs.timing_read()  # clear
+    for _ in range(split_steps):
+        restore()
+        step()
+    per_kernel = hs.timing_read()
+    hs.timing_enable(False)
+    if hs.stream_error() != 0:
+        raise RuntimeError("device error during the instrumented steps")
     step_ms = [a.elapsed_time(b) for a, b in ev]
     mean_ms = statistics.mean(step_ms)
     max_ms = reduce_max(mean_ms, world, dev)
@@ -349,7 +359,7 @@ def main():
     pkt_np = pkt.cpu().numpy()
     active = merge_active_keys(pkt_np, plan["tile"], plan["fan_in"])
     merge_launches, merge_ms = per_kernel.get(mk, (0, 0.0))
-    merge_bytes = 2 * s * sum(active) * args.steps  # each pass reads and writes its active keys
+    merge_bytes = 2 * s * sum(active) * split_steps  # each pass reads and writes its active keys
     achieved = merge_bytes / (merge_ms / 1e3) / 1e9 if merge_ms > 0 else None
     keys_per_launch = sum(active) / max(1, len(active))
     traffic = ncu_traffic(mk, keys_per_launch)
@@ -403,7 +413,8 @@ def main():
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),
-            "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(per_kernel.items())},
+            "kernels_ms_per_step": {k: round(v[1] / split_steps, 4) for k, v in sorted(per_kernel.items())},
+            "kernels_split_steps": split_steps,
             "dominant_kernel": dominant,
             "region_s": region_s,
             "result_sorted": ok_sorted,

@@ -73,7 +73,7 @@ typedef struct {
                            pass merges groups of four adjacent runs, so half the passes over
                            memory; same result bit for bit), or 0 = tuned: the entry of the
                            tuning table (hs_tune_set) for this key type, values, partition
-                           and size bucket, else 4 up to 2^24 keys and 2 above.  Other values
+                           and size bucket, else 4 up to 2^21 keys and 2 above.  Other values
                            return HS_ERR_UNSUPPORTED */
   int stop_after;       /* testing: 0 = whole sort; 1 = stop after the packet step
                            (array holds the stable packet layout); 2 = stop after the

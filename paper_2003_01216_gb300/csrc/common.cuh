@@ -172,6 +172,11 @@ __device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
 __device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// Programmatic dependent launch: every kernel of the library opens with
+// griddep_open(), which waits until the previous kernel of the stream has
+// completed and its memory is visible (a no-op when the launch was not
+// programmatic).  The next kernel is released when this one completes.
+__device__ __forceinline__ void griddep_open() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));

@@ -186,24 +186,16 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
   const bool small = static_cast<uint64_t>(L.max_blocks) * NB <= kPlanSmallEntries &&
                      static_cast<uint64_t>(L.npk) <= kPlanSmallEntries;
 
-  lc.begin("seg_plan");
-  k_seg_plan<<<1, 1024, 0, st>>>(offs, nseg32, n, kTile, tb);
-  HS_TRY(lc.end());
+  HS_TRY(lc.kernel("seg_plan", k_seg_plan, 1, 1024, 0, offs, nseg32, n, kTile, tb));
 
   if constexpr (NB == 1) {
     // no MSD step (ablation): every segment is one packet; the tile sort
     // reads the caller's array directly
     if (small) {
-      lc.begin("plan_small");
-      k_plan_small<1><<<1, 1024, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
-      HS_TRY(lc.end());
+      HS_TRY(lc.kernel("plan_small", (k_plan_small<1>), 1, 1024, 0, nseg32, sort_tile<K, HAS_V>(), tb));
     } else {
-      lc.begin("pkt");
-      k_pkt_whole<<<(nseg32 + 255) / 256, 256, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
-      HS_TRY(lc.end());
-      lc.begin("scan_units");
-      k_scan_units<<<1, 1024, 0, st>>>(L.npk, tb);
-      HS_TRY(lc.end());
+      HS_TRY(lc.kernel("pkt", k_pkt_whole, (nseg32 + 255) / 256, 256, 0, nseg32, sort_tile<K, HAS_V>(), tb));
+      HS_TRY(lc.kernel("scan_units", k_scan_units, 1, 1024, 0, L.npk, tb));
     }
   } else {
     {
@@ -212,47 +204,30 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       auto kern = k_hist<K, NB, kBlock, kIpt>;
       if (!grid) grid = persistent_grid(kern, kBlock, smem);
       for (int img = 0; img < (std::is_same<K, int32_t>::value ? 2 : 1); ++img) {
-        lc.begin(img ? "hist_flip" : "hist");
-        kern<<<grid, kBlock, smem, st>>>(keys, nseg32, kTile, img, tb);
-        HS_TRY(lc.end());
+        HS_TRY(lc.kernel(img ? "hist_flip" : "hist", kern, grid, kBlock, smem, keys, nseg32, kTile, img, tb));
       }
     }
     if (small) {
-      lc.begin("plan_small");
-      k_plan_small<NB><<<1, 1024, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
-      HS_TRY(lc.end());
+      HS_TRY(lc.kernel("plan_small", (k_plan_small<NB>), 1, 1024, 0, nseg32, sort_tile<K, HAS_V>(), tb));
     } else {
-    lc.begin("finalize");
-    k_finalize<NB><<<(nseg32 + 255) / 256, 256, 0, st>>>(nseg32, tb);
-    HS_TRY(lc.end());
+    HS_TRY(lc.kernel("finalize", (k_finalize<NB>), (nseg32 + 255) / 256, 256, 0, nseg32, tb));
     {
       static int grid = 0;
       if (!grid) grid = persistent_grid(k_fold<NB>, 256, 0);
-      lc.begin("fold");
-      k_fold<NB><<<grid, 256, 0, st>>>(nseg32, tb);
-      HS_TRY(lc.end());
+      HS_TRY(lc.kernel("fold", (k_fold<NB>), grid, 256, 0, nseg32, tb));
     }
     // exclusive scan of the (segment, packet, block) counts: absolute positions
     const uint32_t* m_ptr = tb.blk_prefix + nseg;  // total blocks (device)
-    lc.begin("scan_reduce");
-    k_scan_reduce<<<kScanChunks, kScanBlock, 0, st>>>(tb.flat, m_ptr, NB, tb.scan_part);
-    HS_TRY(lc.end());
-    lc.begin("scan_partials");
-    k_scan_partials<<<1, kScanBlock, 0, st>>>(tb.scan_part);
-    HS_TRY(lc.end());
-    lc.begin("scan_down");
-    k_scan_down<<<kScanChunks, kScanBlock, 0, st>>>(tb.flat, m_ptr, NB, tb.scan_part);
-    HS_TRY(lc.end());
+    HS_TRY(lc.kernel("scan_reduce", k_scan_reduce, kScanChunks, kScanBlock, 0, tb.flat, m_ptr, NB,
+                     tb.scan_part));
+    HS_TRY(lc.kernel("scan_partials", k_scan_partials, 1, kScanBlock, 0, tb.scan_part));
+    HS_TRY(lc.kernel("scan_down", k_scan_down, kScanChunks, kScanBlock, 0, tb.flat, m_ptr, NB, tb.scan_part));
     {
       static int grid = 0;
       if (!grid) grid = persistent_grid(k_pkt<NB>, 256, 0);
-      lc.begin("pkt");
-      k_pkt<NB><<<grid, 256, 0, st>>>(nseg32, sort_tile<K, HAS_V>(), tb);
-      HS_TRY(lc.end());
+      HS_TRY(lc.kernel("pkt", (k_pkt<NB>), grid, 256, 0, nseg32, sort_tile<K, HAS_V>(), tb));
     }
-    lc.begin("scan_units");
-    k_scan_units<<<1, 1024, 0, st>>>(L.npk, tb);
-    HS_TRY(lc.end());
+    HS_TRY(lc.kernel("scan_units", k_scan_units, 1, 1024, 0, L.npk, tb));
     }
 
     if constexpr (NB <= 16) {
@@ -261,9 +236,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       const size_t smem = ScatterSmallLayout<K, HAS_V, kBlock, kIpt>::bytes;
       auto kern = k_scatter_small<K, HAS_V, NB, kBlock, kIpt>;
       if (!grid) grid = persistent_grid(kern, kBlock, smem);
-      lc.begin("scatter");
-      kern<<<grid, kBlock, smem, st>>>(keys, vals, kw, vw, nseg32, kTile, tb);
-      HS_TRY(lc.end());
+      HS_TRY(lc.kernel("scatter", kern, grid, kBlock, smem, keys, vals, kw, vw, nseg32, kTile, tb));
     } else {
       const size_t smem = scatter_smem<K, HAS_V, NB>();
       auto kern = k_scatter<K, HAS_V, NB, kBlock, kIpt>;
@@ -272,9 +245,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         attr = true;
       }
-      lc.begin("scatter");
-      kern<<<L.max_blocks, kBlock, smem, st>>>(keys, vals, kw, vw, nseg32, kTile, tb);
-      HS_TRY(lc.end());
+      HS_TRY(lc.kernel("scatter", kern, L.max_blocks, kBlock, smem, keys, vals, kw, vw, nseg32, kTile, tb));
     }
   }
   if (o.stop_after == 1) {
@@ -288,14 +259,12 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       const size_t smem = sort_smem<K, HAS_V>();
       auto kern = k_tilesort<K, HAS_V, kBlock, sort_ipt<K, HAS_V>()>;
       if (!grid) grid = persistent_grid(kern, kBlock, smem);
-      lc.begin("tilesort");
       const bool stuck = (o.debug_flags & 1) != 0;
       const uint64_t limit_ns = stuck ? 2000000ull : 2000000000ull;  // 2 ms when injected, else 2 s
       const K* ts_k = (NB == 1) ? keys : kw;
       const uint32_t* ts_v = (NB == 1) ? vals : vw;
-      kern<<<grid, kBlock, smem, st>>>(ts_k, ts_v, keys, vals, kw, vw, L.npk, o.stop_after == 2 ? 1 : 0,
-                                       stuck ? 1 : 0, limit_ns, tb);
-      HS_TRY(lc.end());
+      HS_TRY(lc.kernel("tilesort", kern, grid, kBlock, smem, ts_k, ts_v, keys, vals, kw, vw, L.npk,
+                       o.stop_after == 2 ? 1 : 0, stuck ? 1 : 0, limit_ns, tb));
     }
     if (o.stop_after == 2) {
       HS_TRY(lc.copy("copy_back", keys, kw, n * sizeof(K)));
@@ -312,12 +281,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       uint32_t* list = reinterpret_cast<uint32_t*>(ws + L.list);
       const int P = o.stop_after >= 3 ? std::min(worst_passes(n, T, 4), o.stop_after - 2) : worst_passes(n, T, 4);
       for (int r = 1; r <= P; ++r) {
-        lc.begin("bound4");
-        ck<<<cgrid, 256, 0, st>>>(keys, kw, recs, list, L.npk, r, tb);
-        HS_TRY(lc.end());
-        lc.begin("merge4");
-        mk<<<mgrid, kMerge4Block, smem, st>>>(keys, vals, kw, vw, recs, list, r, tb);
-        HS_TRY(lc.end());
+        HS_TRY(lc.kernel("bound4", ck, cgrid, 256, 0, keys, kw, recs, list, L.npk, r, tb));
+        HS_TRY(lc.kernel("merge4", mk, mgrid, kMerge4Block, smem, keys, vals, kw, vw, recs, list, r, tb));
       }
     } else {
       static int mgrid = 0, cgrid = 0;
@@ -330,19 +295,14 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       const int P = o.stop_after >= 3 ? std::min(worst_passes(n, sort_tile<K, HAS_V>()), o.stop_after - 2)
                                       : worst_passes(n, sort_tile<K, HAS_V>());
       for (int r = 1; r <= P; ++r) {
-        lc.begin("corank");
-        ck<<<cgrid, 256, 0, st>>>(keys, kw, recs, L.npk, r, tb);
-        HS_TRY(lc.end());
-        lc.begin("merge");
-        mk<<<mgrid, kBlock, smem, st>>>(keys, vals, kw, vw, recs, r, tb);
-        HS_TRY(lc.end());
+        HS_TRY(lc.kernel("corank", ck, cgrid, 256, 0, keys, kw, recs, L.npk, r, tb));
+        HS_TRY(lc.kernel("merge", mk, mgrid, kBlock, smem, keys, vals, kw, vw, recs, r, tb));
       }
     }
     if (o.stop_after >= 3) {  // testing: the state after merge pass r, gathered into the caller's array
-      lc.begin("copy_back_pass");
-      k_copy_back_pass<K, HAS_V, sort_tile<K, HAS_V>()><<<2 * 152, 256, 0, st>>>(keys, vals, kw, vw, L.npk,
-                                                                                o.stop_after - 2, tb);
-      HS_TRY(lc.end());
+      auto kcb = k_copy_back_pass<K, HAS_V, sort_tile<K, HAS_V>()>;
+      HS_TRY(lc.kernel("copy_back_pass", kcb, 2 * 152, 256, 0, keys, vals, kw, vw, L.npk, o.stop_after - 2,
+                       tb));
     }
   }
   if (o.d_packet_offsets_out)

@@ -145,8 +145,8 @@ int tuned_fan_in(int dtype, bool has_vals, int partition, size_t n) {
     if (it != g_tune.end()) return it->second;
   }
   // built-in rule from one GB300: four-way passes win while passes are short
-  // (launch- and latency-bound), two-way passes above 2^24 keys
-  return n <= (static_cast<size_t>(1) << 24) ? 4 : 2;
+  // (launch- and latency-bound), two-way passes above 2^21 keys
+  return n <= (static_cast<size_t>(1) << 21) ? 4 : 2;
 }
 
 hs_status check_opts(const hs_opts* opts, hs_opts* o) {

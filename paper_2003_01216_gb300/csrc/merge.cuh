@@ -46,6 +46,7 @@ __device__ __forceinline__ void corank2(const K* __restrict__ A, uint32_t la, co
 template <class K, int TILE>
 __global__ void k_corank(const K* __restrict__ ku, const K* __restrict__ kw, MergeRec* __restrict__ recs,
                          uint32_t npk, int r, Tables tb) {
+  griddep_open();
   if (static_cast<uint32_t>(r) > tb.pass_ctl[0]) return;  // no packet needs pass r
   const uint32_t total = tb.unit_prefix[npk];
   const int lane = threadIdx.x & 31;
@@ -141,6 +142,7 @@ template <class K, bool HAS_V, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_merge(K* ku, uint32_t* vu, K* kw, uint32_t* vw,
                                                                  const MergeRec* __restrict__ recs, int r,
                                                                  Tables tb) {
+  griddep_open();
   constexpr int TILE = BLOCK * IPT;
   constexpr bool SEP = separate_out<K, HAS_V, TILE>();
   constexpr size_t KB = (region_elems(TILE) * sizeof(K) + 127) & ~size_t(127);

@@ -63,6 +63,7 @@ __device__ __forceinline__ uint32_t samples_before(uint32_t x) {
 template <class K, int TILE, int SPT>
 __global__ void k_bound4(const K* __restrict__ ku, const K* __restrict__ kw, Rec4* __restrict__ recs,
                          uint32_t* __restrict__ list, uint32_t npk, int r, Tables tb) {
+  griddep_open();
   constexpr int G = kSamplesPerChunk;
   constexpr uint32_t S = sample_gap<TILE, SPT>();
   constexpr uint32_t PER_TILE = SPT * G;  // sample slots per tile
@@ -326,6 +327,7 @@ template <class K, bool HAS_V, int BLOCK, int MINB, int CMAX>
 __global__ void __launch_bounds__(BLOCK, MINB) k_merge4(K* ku, uint32_t* vu, K* kw, uint32_t* vw,
                                                          const Rec4* __restrict__ recs,
                                                          const uint32_t* __restrict__ list, int r, Tables tb) {
+  griddep_open();
   constexpr size_t KB = merge4_region_bytes<K, HAS_V, CMAX>();
   constexpr size_t SB = merge4_buffer_bytes<K, HAS_V, CMAX>();
   extern __shared__ __align__(128) unsigned char s_raw[];

@@ -42,6 +42,7 @@ namespace hs {
 // ---------------------------------------------------------------------------
 static __global__ void k_seg_plan(const uint64_t* __restrict__ offs, uint32_t nseg, uint64_t n, uint32_t part_tile,
                            Tables tb) {
+  griddep_open();
   __shared__ uint32_t s_bad;
   __shared__ uint32_t s_carry;
   __shared__ uint32_t s_warp[32];
@@ -187,6 +188,7 @@ __device__ __forceinline__ void hist_count_block(const K* keysrc, bool from_smem
 template <class K, int NB, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint32_t nseg, uint32_t part_tile,
                                                  int img, Tables tb) {
+  griddep_open();
   using U = typename KT<K>::U;
   constexpr int NW = BLOCK / kWarp;
   constexpr int TILE = BLOCK * IPT;
@@ -291,6 +293,7 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
 // ---------------------------------------------------------------------------
 template <int NB>
 __global__ void k_finalize(uint32_t nseg, Tables tb) {
+  griddep_open();
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
   const uint32_t neg = tb.seg_neg[s];
@@ -306,6 +309,7 @@ __global__ void k_finalize(uint32_t nseg, Tables tb) {
 // ---------------------------------------------------------------------------
 template <int NB>
 __global__ void k_fold(uint32_t nseg, Tables tb) {
+  griddep_open();
   const uint32_t total = tb.blk_prefix[nseg];
   const uint64_t m = static_cast<uint64_t>(total) * NB;
   for (uint64_t idx = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; idx < m;
@@ -337,6 +341,7 @@ __global__ void k_fold(uint32_t nseg, Tables tb) {
 // ---------------------------------------------------------------------------
 template <int NB>
 __global__ void k_pkt(uint32_t nseg, uint32_t tile, Tables tb) {
+  griddep_open();
   const uint64_t m = static_cast<uint64_t>(nseg) * NB;
   for (uint64_t idx = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; idx < m;
        idx += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
@@ -361,6 +366,7 @@ __global__ void k_pkt(uint32_t nseg, uint32_t tile, Tables tb) {
 // k_pkt_whole: no MSD step (ablation): every segment is one packet.
 // ---------------------------------------------------------------------------
 static __global__ void k_pkt_whole(uint32_t nseg, uint32_t tile, Tables tb) {
+  griddep_open();
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
     const uint64_t start = tb.seg_off[s], end = tb.seg_off[s + 1];
     tb.pkt_off[s] = start;
@@ -376,6 +382,7 @@ static __global__ void k_pkt_whole(uint32_t nseg, uint32_t tile, Tables tb) {
 // k_scan_units: in-place exclusive scan of unit_prefix[0..m), total to [m].
 // ---------------------------------------------------------------------------
 static __global__ void k_scan_units(uint32_t m, Tables tb) {
+  griddep_open();
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
@@ -463,6 +470,7 @@ constexpr uint32_t kPlanSmallEntries = 1u << 16;
 
 template <int NB>
 __global__ void __launch_bounds__(1024) k_plan_small(uint32_t nseg, uint32_t tile, Tables tb) {
+  griddep_open();
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
   const uint32_t tid = threadIdx.x, nt = blockDim.x;
@@ -549,6 +557,7 @@ template <class K, bool HAS_V, int NB, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK, 2) k_scatter(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                                                     K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                     uint32_t nseg, uint32_t part_tile, Tables tb) {
+  griddep_open();
   constexpr int NW = BLOCK / kWarp;
   constexpr int TILE = BLOCK * IPT;
   constexpr int NBX = NB + 1;  // + a dummy packet for lanes past the end
@@ -695,6 +704,7 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_sc
                                                             const uint32_t* __restrict__ vals_in,
                                                             K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                             uint32_t nseg, uint32_t part_tile, Tables tb) {
+  griddep_open();
   static_assert(NB <= 16 && IPT <= 15, "4-bit local counts; 16-bit block counts");
   using LY = ScatterSmallLayout<K, HAS_V, BLOCK, IPT>;
   constexpr int NW = BLOCK / kWarp;

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "hsort.h"
 
@@ -49,8 +50,38 @@ class Launcher {
     }
     return HS_OK;
   }
+  // One kernel launch.  When the previous operation this launcher put on the
+  // stream was a kernel (and no timing events sit between them), the launch
+  // is a programmatic dependent launch: the launch is processed while the
+  // previous kernel runs and its CTAs start as soon as that kernel completes;
+  // every kernel of the library opens with griddepcontrol.wait, which returns
+  // once the previous kernel has completed and its writes are visible.  No
+  // kernel releases its dependents early: CTAs of the next kernel parked on
+  // the SMs while a long persistent kernel runs cost more than they save.
+  template <class... KArgs, class... Args>
+  hs_status kernel(const char* name, void (*f)(KArgs...), dim3 grid, dim3 block, size_t smem, Args&&... args) {
+    begin(name);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st_;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = (prev_kernel_ && !t0_) ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, f, std::forward<Args>(args)...);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return HS_ERR_CUDA;
+    }
+    prev_kernel_ = true;
+    return end();
+  }
   hs_status memset(const char* name, void* p, int v, size_t bytes) {
     if (!bytes) return HS_OK;
+    prev_kernel_ = false;
     begin(name);
     cudaError_t e = cudaMemsetAsync(p, v, bytes, st_);
     if (e != cudaSuccess) {
@@ -61,6 +92,7 @@ class Launcher {
   }
   hs_status copy(const char* name, void* dst, const void* src, size_t bytes) {
     if (!bytes) return HS_OK;
+    prev_kernel_ = false;
     begin(name);
     cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st_);
     if (e != cudaSuccess) {
@@ -74,6 +106,7 @@ class Launcher {
   cudaStream_t st_;
   const char* name_ = "";
   cudaEvent_t t0_ = nullptr;
+  bool prev_kernel_ = false;
 };
 
 // Entry points of the per-key-type translation units.

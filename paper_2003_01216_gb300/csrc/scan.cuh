@@ -45,6 +45,7 @@ __device__ __forceinline__ void chunk_range(uint64_t m, uint32_t c, uint64_t& lo
 static __global__ void __launch_bounds__(kScanBlock) k_scan_reduce(const uint32_t* __restrict__ a,
                                                                     const uint32_t* __restrict__ m_ptr, uint32_t mult,
                                                                     uint32_t* __restrict__ partials) {
+  griddep_open();
   __shared__ uint32_t s_warp[32];
   const uint64_t m = static_cast<uint64_t>(*m_ptr) * mult;
   uint64_t lo, hi;
@@ -63,6 +64,7 @@ static __global__ void __launch_bounds__(kScanBlock) k_scan_reduce(const uint32_
 
 // 2. partials -> exclusive prefix (one CTA)
 static __global__ void __launch_bounds__(kScanBlock) k_scan_partials(uint32_t* __restrict__ partials) {
+  griddep_open();
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
   if (threadIdx.x == 0) s_carry = 0;
@@ -82,6 +84,7 @@ static __global__ void __launch_bounds__(kScanBlock) k_scan_partials(uint32_t* _
 static __global__ void __launch_bounds__(kScanBlock) k_scan_down(uint32_t* __restrict__ a,
                                                                   const uint32_t* __restrict__ m_ptr, uint32_t mult,
                                                                   const uint32_t* __restrict__ partials) {
+  griddep_open();
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
   const uint64_t m = static_cast<uint64_t>(*m_ptr) * mult;

@@ -12,6 +12,7 @@ template <class K, bool HAS_V, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, const uint32_t* __restrict__ vw, K* ku,
                                                      uint32_t* vu, K* kw_out, uint32_t* vw_out, uint32_t npk,
                                                      int force_w, int debug_stuck, uint64_t limit_ns, Tables tb) {
+  griddep_open();
   constexpr int TILE = BLOCK * IPT;
   constexpr int RE = region_elems(TILE);
   extern __shared__ __align__(128) unsigned char s_raw[];
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
 template <class K, bool HAS_V, int TILE>
 __global__ void k_copy_back_pass(K* ku, uint32_t* vu, const K* __restrict__ kw, const uint32_t* __restrict__ vw,
                                  uint32_t npk, int r, Tables tb) {
+  griddep_open();
   const uint32_t total = tb.unit_prefix[npk];
   for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
     const uint32_t p = find_pkt(tb.unit_prefix, npk, u);

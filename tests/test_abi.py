@@ -130,8 +130,8 @@ def test_tuning_table_and_default_rule():
     lib = N.lib()
     tune.clear()
     try:
-        # built-in rule: four-way passes up to 2^24 keys, two-way above
-        assert tune.get(N.HS_INT32, 1 << 20) == 4 and tune.get(N.HS_INT32, (1 << 24) + 1) == 2
+        # built-in rule: four-way passes up to 2^21 keys, two-way above
+        assert tune.get(N.HS_INT32, 1 << 21) == 4 and tune.get(N.HS_INT32, (1 << 21) + 1) == 2
         assert hs.plan(N.HS_INT32, 1 << 20)["fan_in"] == 4 and hs.plan(N.HS_INT32, 1 << 28)["fan_in"] == 2
         # a table entry overrides the rule for its bucket only (bucket = ceil(log2 n))
         tune.set_entry(N.HS_INT32, False, 10, 28, 4)
@@ -159,16 +159,16 @@ def test_tuning_cache_roundtrip(tmp_path):
     from paper_2003_01216_gb300 import tune
     tune.clear()
     try:
-        entries = [{"dtype": "uint64", "has_vals": True, "partition": 10, "log2n": 22, "fan_in": 2,
+        entries = [{"dtype": "uint64", "has_vals": True, "partition": 10, "log2n": 20, "fan_in": 2,
                     "ms": {"2": 1.0, "4": 1.5}},
                    {"dtype": "int32", "has_vals": False, "partition": 256, "log2n": 30, "fan_in": 4,
                     "ms": {"2": 9.0, "4": 8.0}}]
         path = str(tmp_path / "tune.json")
         tune.save(path, entries, device="GPU A")
         assert tune.load(path, device="GPU B") == 0            # measured on another GPU: skipped
-        assert tune.get(N.HS_UINT64, 1 << 22, has_vals=True) == 4  # rule still in force
+        assert tune.get(N.HS_UINT64, 1 << 20, has_vals=True) == 4  # rule still in force
         assert tune.load(path, device="GPU A") == 2
-        assert tune.get(N.HS_UINT64, 1 << 22, has_vals=True) == 2
+        assert tune.get(N.HS_UINT64, 1 << 20, has_vals=True) == 2
         assert tune.get(N.HS_INT32, 1 << 30, partition=256) == 4
         assert tune.size_bucket(1) == 0 and tune.size_bucket(1 << 20) == 20 and tune.size_bucket((1 << 20) + 1) == 21
     finally:
