@@ -278,7 +278,6 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 size_t workspace_bytes(size_t kb, size_t n, bool has_vals, size_t nseg, int nb) {
   return make_layout(kb, n, has_vals, nseg, nb).total;
 }
-int plan_passes(size_t n, size_t tile) { return worst_passes(n, tile); }
 
 }  // namespace hs
 

@@ -15,8 +15,11 @@
 //                 first position in every packet
 //   k_pkt         packet offsets and tiles per packet
 //   k_scan_units  exclusive scan of the tiles per packet (one CTA)
-//   k_scatter     stable scatter into packets (one read + one write of the
-//                 keys and values; no block waits on another)
+//   (small calls run k_finalize .. k_scan_units as one CTA: k_plan_small)
+//   k_scatter_small / k_scatter
+//                 stable scatter into packets (one read + one write of the
+//                 keys and values; no block waits on another): persistent with
+//                 bulk copies for up to 16 packets, one CTA per block for 256
 //
 // The class trick: the packet of a key depends on the class (digit count D,
 // or bit length B) of the LARGEST key image of its array, which no block
@@ -126,7 +129,7 @@ __device__ __forceinline__ uint32_t find_seg(const uint32_t* __restrict__ pre, u
 //            segment holds a negative key)
 // ---------------------------------------------------------------------------
 template <class K, int NB, int BLOCK, int IPT>
-__device__ __forceinline__ void hist_count_block(const K* keysrc, bool from_smem, uint32_t cnt, bool flip, int img,
+__device__ __forceinline__ void hist_count_block(const K* keysrc, uint32_t cnt, bool flip, int img,
                                                  uint32_t* s_cnt, typename KT<K>::U* s_max, uint32_t& s_neg,
                                                  int& cls_out) {
   using U = typename KT<K>::U;
@@ -142,7 +145,6 @@ __device__ __forceinline__ void hist_count_block(const K* keysrc, bool from_smem
     u[j] = (full || i < cnt) ? KT<K>::image(keysrc[i], flip) : U(0);
     m = max(m, u[j]);
   }
-  (void)from_smem;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, static_cast<U>(__shfl_xor_sync(0xffffffffu, m, o)));
   if (lane == 0) s_max[wid] = m;
@@ -271,11 +273,11 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
         return;
       }
       const K* region = reinterpret_cast<const K*>(s_raw + st * STAGE) + phase_of(keys + beg);
-      hist_count_block<K, NB, BLOCK, IPT>(region, true, cnt, false, 0, s_cnt, s_max, s_neg, cls);
+      hist_count_block<K, NB, BLOCK, IPT>(region, cnt, false, 0, s_cnt, s_max, s_neg, cls);
       st ^= 1;
     } else {
       if (!tb.seg_neg[seg]) continue;  // block-uniform
-      hist_count_block<K, NB, BLOCK, IPT>(keys + beg, false, cnt, true, 1, s_cnt, s_max, s_neg, cls);
+      hist_count_block<K, NB, BLOCK, IPT>(keys + beg, cnt, true, 1, s_cnt, s_max, s_neg, cls);
     }
     for (int q = tid; q < NB; q += BLOCK) tb.cnt_raw[static_cast<size_t>(b) * NB + q] = s_cnt[q];
     if (tid == 0) {

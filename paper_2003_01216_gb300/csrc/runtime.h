@@ -117,6 +117,5 @@ hs_status run_sort_u32(void* keys, uint32_t* vals, size_t n, size_t nseg, const 
 hs_status run_sort_u64(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
                        char* ws, uint32_t* err, cudaStream_t st);
 size_t workspace_bytes(size_t key_bytes, size_t n, bool has_vals, size_t nseg, int nb);
-int plan_passes(size_t n, size_t tile);
 
 }  // namespace hs
