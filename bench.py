@@ -78,26 +78,44 @@ def barrier(world: int, device=None) -> None:
 # --------------------------------------------------------------------------
 # clocks sampled during the timed region
 # --------------------------------------------------------------------------
-CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+CLOCK_Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
            "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
 class ClockSampler:
+    """nvidia-smi sampling every 20 ms.  Entering waits (up to 5 s) for the
+    first sample, so sampling is running when the timed region starts; mark()
+    and done() bracket the region, and summary() keeps the samples taken inside
+    it (or, when the region is shorter than the period, the ones nearest it)."""
+
+    PERIOD_MS = 20
+
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
         self.path = os.path.join("/tmp", f"hs_clocks_{os.getpid()}.csv")
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.idx), "-lms", "100"], stdout=self.f,
+                                          "-i", str(self.idx), "-lms", str(self.PERIOD_MS)], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
+            t_end = time.time() + 5.0
+            while time.time() < t_end and not self._rows():
+                time.sleep(0.02)
         except Exception:  # noqa: BLE001 - no nvidia-smi: clocks unknown
             self.proc = None
         return self
+
+    def mark(self):
+        self.t0 = time.time()
+
+    def done(self):
+        self.t1 = time.time()
+        time.sleep(2.5 * self.PERIOD_MS / 1e3)  # the sample that closes the region
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -108,27 +126,49 @@ class ClockSampler:
                 self.proc.kill()
             self.f.close()
 
+    def _rows(self) -> list[tuple[float, list[str]]]:
+        import datetime
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 10 or not parts[2].replace(".", "").isdigit():
+                        continue
+                    try:
+                        ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    except ValueError:
+                        continue
+                    rows.append((ts, parts[1:]))
+        except OSError:
+            pass
+        return rows
+
     def summary(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
-                    rows.append(parts)
-        if not rows:
+        allrows = self._rows()
+        if not allrows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
-        sm = [float(r[1]) for r in rows]
+        t0 = self.t0 if self.t0 is not None else allrows[0][0]
+        t1 = self.t1 if self.t1 is not None else allrows[-1][0]
+        inside = [r for t, r in allrows if t0 <= t <= t1]
+        where = "inside the timed region"
+        if not inside:  # region shorter than the period: the samples nearest it
+            near = sorted(allrows, key=lambda tr: min(abs(tr[0] - t0), abs(tr[0] - t1)))[:2]
+            inside = [r for _, r in near]
+            where = "nearest the timed region (region shorter than the sampling period)"
+        sm = [float(r[1]) for r in inside]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
+        for r in inside:
             for name, v in zip(names, r[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
-                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
-                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+        pw = [float(r[3]) for r in inside if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(inside[0][2]), "reasons": sorted(reasons),
+                "samples": len(inside), "samples_where": where, "period_ms": self.PERIOD_MS,
+                "power_w_max": max(pw) if pw else None}
 
 
 # --------------------------------------------------------------------------
@@ -321,6 +361,7 @@ def main():
         barrier(world, dev)
         torch.cuda.synchronize()
         l0 = hs.kernel_launches()
+        clk.mark()
         t_region = time.perf_counter()
         for i in range(args.steps):
             restore()
@@ -330,6 +371,7 @@ def main():
         torch.cuda.synchronize()
         barrier(world, dev)
         region_s = time.perf_counter() - t_region
+        clk.done()
         launches = hs.kernel_launches() - l0
     err = hs.stream_error()
     if err != 0:
@@ -450,12 +492,14 @@ def run_batch(args, rank, world, dev, dist_name):
             barrier(world, dev)
             torch.cuda.synchronize()
             l0 = hs.kernel_launches()
+            clk.mark()
             for i in range(args.steps):
                 work.copy_(pristine)
                 ev[i][0].record(st)
                 hs.sort_batch(work, offs, graph=True)
                 ev[i][1].record(st)
             torch.cuda.synchronize()
+            clk.done()
             launches = hs.kernel_launches() - l0
         ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
         ok = hs.stream_error(st) == 0
@@ -503,7 +547,9 @@ def run_serve(args, rank, world, dev):
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
         barrier(world, dev)
+        clk.mark()
         st = serve.Server(slots=8, budget_bytes=64 << 30, seed=rank).run(reqs)
+        clk.done()
         barrier(world, dev)
     ser = None if args.no_serial else serve.serial(reqs, seed=rank)
     keys_s = reduce_max(-st["keys_per_s"], world, dev)  # min over ranks
