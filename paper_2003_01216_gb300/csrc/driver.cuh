@@ -41,6 +41,10 @@ inline int sort_tile_for(size_t key_bytes, bool has_vals) {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 constexpr int kMaxPasses = 64;
+// Lanes per co-rank search: more lanes per search when a pass has few merge
+// blocks (its co-rank kernel is then bound by the latency of the search
+// chain), one thread per merge block when it has many.
+inline int corank_group(size_t units) { return units <= 4096 ? 16 : (units <= 16384 ? 4 : 1); }
 constexpr int kMerge4Spt = 2;  // fan-in-4 merge: chunk slots per tile (average chunk = tile / slots)  // pass-control words (n < 2^32 needs at most 32 passes)
 
 struct Layout {
@@ -167,6 +171,14 @@ inline int persistent_grid(Kern kern, int block, size_t smem) {
   return sms * occ;
 }
 
+template <class K, int T, int G>
+hs_status launch_corank(Launcher& lc, K* keys, K* kw, MergeRec* recs, uint32_t npk, int r, const Tables& tb) {
+  static int grid = 0;
+  auto ck = k_corank<K, T, G>;
+  if (!grid) grid = persistent_grid(ck, 256, 0);
+  return lc.kernel("corank", ck, grid, 256, 0, keys, kw, recs, npk, r, tb);
+}
+
 // One sort call.  keys/vals: the caller's arrays (U).  offs: batch offsets
 // (device) or nullptr for one segment.  ws: work space of at least
 // make_layout(...).total bytes.
@@ -192,7 +204,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     // no MSD step (ablation): every segment is one packet; the tile sort
     // reads the caller's array directly
     if (small) {
-      HS_TRY(lc.kernel("plan_small", (k_plan_small<1>), 1, 1024, 0, nseg32, sort_tile<K, HAS_V>(), tb));
+      HS_TRY(lc.kernel("plan_small", (k_plan_small<1>), 1, kPlanThreads, 0, nseg32, sort_tile<K, HAS_V>(), tb));
     } else {
       HS_TRY(lc.kernel("pkt", k_pkt_whole, (nseg32 + 255) / 256, 256, 0, nseg32, sort_tile<K, HAS_V>(), tb));
       HS_TRY(lc.kernel("scan_units", k_scan_units, 1, 1024, 0, L.npk, tb));
@@ -208,7 +220,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       }
     }
     if (small) {
-      HS_TRY(lc.kernel("plan_small", (k_plan_small<NB>), 1, 1024, 0, nseg32, sort_tile<K, HAS_V>(), tb));
+      HS_TRY(lc.kernel("plan_small", (k_plan_small<NB>), 1, kPlanThreads, 0, nseg32, sort_tile<K, HAS_V>(), tb));
     } else {
     HS_TRY(lc.kernel("finalize", (k_finalize<NB>), (nseg32 + 255) / 256, 256, 0, nseg32, tb));
     {
@@ -235,7 +247,10 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       static int grid = 0;
       const size_t smem = ScatterSmallLayout<K, HAS_V, kBlock, kIpt>::bytes;
       auto kern = k_scatter_small<K, HAS_V, NB, kBlock, kIpt>;
-      if (!grid) grid = persistent_grid(kern, kBlock, smem);
+      if (!grid) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        grid = persistent_grid(kern, kBlock, smem);
+      }
       HS_TRY(lc.kernel("scatter", kern, grid, kBlock, smem, keys, vals, kw, vw, nseg32, kTile, tb));
     } else {
       const size_t smem = scatter_smem<K, HAS_V, NB>();
@@ -285,17 +300,18 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
         HS_TRY(lc.kernel("merge4", mk, mgrid, kMerge4Block, smem, keys, vals, kw, vw, recs, list, r, tb));
       }
     } else {
-      static int mgrid = 0, cgrid = 0;
+      static int mgrid = 0;
       const size_t smem = merge_smem<K, HAS_V>();
       auto mk = k_merge<K, HAS_V, kBlock, sort_ipt<K, HAS_V>()>;
-      auto ck = k_corank<K, sort_tile<K, HAS_V>()>;
+      constexpr int T = sort_tile<K, HAS_V>();
       if (!mgrid) mgrid = persistent_grid(mk, kBlock, smem);
-      if (!cgrid) cgrid = persistent_grid(ck, 256, 0);
       MergeRec* recs = reinterpret_cast<MergeRec*>(ws + L.recs);
-      const int P = o.stop_after >= 3 ? std::min(worst_passes(n, sort_tile<K, HAS_V>()), o.stop_after - 2)
-                                      : worst_passes(n, sort_tile<K, HAS_V>());
+      const int P = o.stop_after >= 3 ? std::min(worst_passes(n, T), o.stop_after - 2) : worst_passes(n, T);
+      const int G = corank_group((n + T - 1) / T);
       for (int r = 1; r <= P; ++r) {
-        HS_TRY(lc.kernel("corank", ck, cgrid, 256, 0, keys, kw, recs, L.npk, r, tb));
+        if (G == 16) HS_TRY((launch_corank<K, T, 16>(lc, keys, kw, recs, L.npk, r, tb)));
+        else if (G == 4) HS_TRY((launch_corank<K, T, 4>(lc, keys, kw, recs, L.npk, r, tb)));
+        else HS_TRY((launch_corank<K, T, 1>(lc, keys, kw, recs, L.npk, r, tb)));
         HS_TRY(lc.kernel("merge", mk, mgrid, kBlock, smem, keys, vals, kw, vw, recs, r, tb));
       }
     }

@@ -43,40 +43,119 @@ __device__ __forceinline__ void corank2(const K* __restrict__ A, uint32_t la, co
   r1 = lo1;
 }
 
-template <class K, int TILE>
+// Record of one merge block from its geometry and the co-ranks i0, i1 of its
+// first and one-past-last output.
+__device__ __forceinline__ MergeRec make_rec(const MergeGeom& g, bool srcw, uint32_t i0, uint32_t i1) {
+  const uint64_t abs_a = g.pstart + g.a_start;
+  MergeRec rec;
+  rec.a = (abs_a + i0) | (srcw ? kSrcW : 0ull);
+  rec.b = abs_a + g.a_len + (g.diag0 - i0);
+  rec.out = abs_a + g.diag0;
+  rec.la = i1 - i0;
+  rec.lb = g.cnt - rec.la;
+  return rec;
+}
+
+// Records of the active lanes, packed densely at pass_ctl[r] (their order
+// does not matter).  Called by all 32 lanes.
+__device__ __forceinline__ void push_recs(bool writer, const MergeRec& rec, MergeRec* recs, uint32_t* ctr, int lane) {
+  const uint32_t mask = __ballot_sync(0xffffffffu, writer);
+  if (mask) {
+    uint32_t slot = 0;
+    if (lane == __ffs(mask) - 1) slot = atomicAdd(ctr, __popc(mask));
+    slot = __shfl_sync(0xffffffffu, slot, __ffs(mask) - 1);
+    if (writer) recs[slot + __popc(mask & ((1u << lane) - 1u))] = rec;
+  }
+}
+
+// G == 1: one thread per merge block, its two searches interleaved.
+// G > 1: G lanes per search, 2G lanes per merge block: every step the G lanes
+// probe G evenly spaced points of the remaining interval at once, so the
+// interval shrinks (G + 1)-fold per dependent load instead of 2-fold (few
+// merge blocks: the pass is bound by the latency of the search chain).
+template <class K, int TILE, int G>
 __global__ void k_corank(const K* __restrict__ ku, const K* __restrict__ kw, MergeRec* __restrict__ recs,
                          uint32_t npk, int r, Tables tb) {
+  static_assert(G == 1 || (G >= 2 && G <= 16 && (G & (G - 1)) == 0), "group of 1, 2, 4, 8 or 16 lanes");
   griddep_open();
   if (static_cast<uint32_t>(r) > tb.pass_ctl[0]) return;  // no packet needs pass r
   const uint32_t total = tb.unit_prefix[npk];
   const int lane = threadIdx.x & 31;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  // warp-uniform trip count: lanes past the end take part in the ballot
-  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
-    const uint32_t u = base + lane;
-    MergeGeom g;
-    MergeRec rec{0, 0, 0, 0, 0};
-    const bool active = u < total && merge_geom<TILE>(tb, npk, u, r, g);
-    if (active) {
-      const bool srcw = ((g.passes - r + 1) & 1) != 0;  // the buffer holding pass r-1
-      const K* A = (srcw ? kw : ku) + g.pstart + g.a_start;
-      const K* B = A + g.a_len;
-      uint32_t i0, i1;
-      corank2(A, g.a_len, B, g.b_len, g.diag0, g.diag0 + g.cnt, i0, i1);
-      const uint64_t abs_a = g.pstart + g.a_start;
-      rec.a = (abs_a + i0) | (srcw ? kSrcW : 0ull);
-      rec.b = abs_a + g.a_len + (g.diag0 - i0);
-      rec.out = abs_a + g.diag0;
-      rec.la = i1 - i0;
-      rec.lb = g.cnt - rec.la;
+  if constexpr (G == 1) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // warp-uniform trip count: lanes past the end take part in the ballot
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+      const uint32_t u = base + lane;
+      MergeGeom g;
+      MergeRec rec{0, 0, 0, 0, 0};
+      const bool active = u < total && merge_geom<TILE>(tb, npk, u, r, g);
+      if (active) {
+        const bool srcw = ((g.passes - r + 1) & 1) != 0;  // the buffer holding pass r-1
+        const K* A = (srcw ? kw : ku) + g.pstart + g.a_start;
+        const K* B = A + g.a_len;
+        uint32_t i0, i1;
+        corank2(A, g.a_len, B, g.b_len, g.diag0, g.diag0 + g.cnt, i0, i1);
+        rec = make_rec(g, srcw, i0, i1);
+      }
+      push_recs(active, rec, recs, &tb.pass_ctl[r], lane);
     }
-    // active blocks only, packed densely (their order does not matter)
-    const uint32_t mask = __ballot_sync(0xffffffffu, active);
-    if (mask) {
-      uint32_t slot = 0;
-      if (lane == __ffs(mask) - 1) slot = atomicAdd(&tb.pass_ctl[r], __popc(mask));
-      slot = __shfl_sync(0xffffffffu, slot, __ffs(mask) - 1);
-      if (active) recs[slot + __popc(mask & ((1u << lane) - 1u))] = rec;
+  } else {
+    constexpr int L = 2 * G;     // lanes per merge block
+    constexpr int BPW = 32 / L;  // merge blocks per warp
+    const int sub = lane % L, q = sub / G, j = sub % G;
+    const int gbase = lane - j;  // first lane of this lane's search group
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = warp; w * BPW < total; w += nwarps) {  // warp-uniform
+      const uint32_t u = w * BPW + lane / L;
+      MergeGeom g;
+      const bool active = u < total && merge_geom<TILE>(tb, npk, u, r, g);
+      const K* A = ku;
+      const K* B = ku;
+      bool srcw = false;
+      uint32_t d = 0, lo = 0, hi = 0;
+      if (active) {
+        srcw = ((g.passes - r + 1) & 1) != 0;
+        A = (srcw ? kw : ku) + g.pstart + g.a_start;
+        B = A + g.a_len;
+        d = g.diag0 + (q ? g.cnt : 0u);  // q = 0: first output, q = 1: one past the last
+        lo = d > g.b_len ? d - g.b_len : 0u;
+        hi = min(d, g.a_len);
+      }
+      // invariant: the co-rank lies in [lo, hi]; probe m is "taken" (the
+      // co-rank exceeds m) when B[d - 1 - m] does not precede A[m]
+      while (__any_sync(0xffffffffu, lo < hi)) {
+        const uint32_t n = hi - lo;
+        bool taken = false;
+        if (n > 0) {
+          const uint32_t m = (n <= static_cast<uint32_t>(G))
+                                 ? lo + j
+                                 : lo + static_cast<uint32_t>((static_cast<uint64_t>(j + 1) * n) / (G + 1));
+          if (m < hi) taken = !(B[d - 1 - m] < A[m]);
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, taken);
+        const uint32_t k = __popc((bal >> gbase) & ((1u << G) - 1u));
+        if (n > 0) {
+          if (n <= static_cast<uint32_t>(G)) {  // every point of the interval probed
+            lo += k;
+            hi = lo;
+          } else {  // taken probes are a prefix (the predicate is monotone)
+            const uint32_t nlo = k ? lo + static_cast<uint32_t>((static_cast<uint64_t>(k) * n) / (G + 1)) + 1u : lo;
+            const uint32_t nhi =
+                (k < static_cast<uint32_t>(G)) ? lo + static_cast<uint32_t>((static_cast<uint64_t>(k + 1) * n) / (G + 1))
+                                               : hi;
+            lo = nlo;
+            hi = nhi;
+          }
+        }
+      }
+      const int l0 = lane - sub;  // lane holding the block's first co-rank
+      const uint32_t i0 = __shfl_sync(0xffffffffu, lo, l0);
+      const uint32_t i1 = __shfl_sync(0xffffffffu, lo, l0 + G);
+      const bool writer = active && sub == 0;
+      MergeRec rec{0, 0, 0, 0, 0};
+      if (writer) rec = make_rec(g, srcw, i0, i1);
+      push_recs(writer, rec, recs, &tb.pass_ctl[r], lane);
     }
   }
 }

@@ -470,10 +470,53 @@ __device__ __forceinline__ void cta_exclusive_scan(uint32_t* a, uint32_t m, uint
 // ---------------------------------------------------------------------------
 constexpr uint32_t kPlanSmallEntries = 1u << 16;
 
+// Count of packet p of block b under class C when the block's own class cb
+// differs from C (see k_fold).
 template <int NB>
-__global__ void __launch_bounds__(1024) k_plan_small(uint32_t nseg, uint32_t tile, Tables tb) {
+__device__ __forceinline__ uint32_t fold_other(const Tables& tb, uint32_t b, uint32_t p, uint32_t cb, uint32_t C) {
+  const uint32_t* raw = tb.cnt_raw + static_cast<size_t>(b) * NB;
+  uint32_t v = 0;
+  if constexpr (NB == 10) {
+    if (p == 0) {  // every key of the block is below 10^(C-1): packet 0
+#pragma unroll
+      for (int t = 0; t < 10; ++t) v += raw[t];
+    }
+  } else {
+    const uint32_t d = (C > 8 ? C - 8 : 0) - (cb > 8 ? cb - 8 : 0);
+    const uint32_t l = p << d, h = min(static_cast<uint32_t>(NB), (p + 1) << d);
+    for (uint32_t t = l; t < h; ++t) v += raw[t];
+  }
+  return v;
+}
+
+// Entry e of the (segment, packet, block) array: its block b, packet p and
+// the segment's class C.  Segment s owns entries
+// [blk_prefix[s] * NB, blk_prefix[s + 1] * NB), packet-major inside it.
+template <int NB>
+__device__ __forceinline__ void folded_pos(const Tables& tb, uint32_t nseg, uint32_t e, uint32_t& b, uint32_t& p,
+                                           uint32_t& C) {
+  uint32_t lo = 0, hi = nseg;  // last s with blk_prefix[s] * NB <= e
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (tb.blk_prefix[mid] * NB <= e) lo = mid; else hi = mid;
+  }
+  const uint32_t first = tb.blk_prefix[lo], nb_s = tb.blk_prefix[lo + 1] - first;
+  const uint32_t rel = e - first * NB;
+  p = rel / nb_s;
+  b = first + (rel - p * nb_s);
+  C = tb.seg_class[lo];
+}
+
+constexpr int kPlanThreads = 1024;
+constexpr int kPer = 8;                          // entries per thread per chunk
+constexpr int kChunk = kPlanThreads * kPer;
+__device__ __forceinline__ uint32_t chunk_pad(uint32_t i) { return i + (i >> 5); }
+
+template <int NB>
+__global__ void __launch_bounds__(kPlanThreads) k_plan_small(uint32_t nseg, uint32_t tile, Tables tb) {
   griddep_open();
   __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_chunk[kChunk + kChunk / 32];  // one pad word per 32: conflict-free raking
   __shared__ uint32_t s_carry;
   const uint32_t tid = threadIdx.x, nt = blockDim.x;
   const uint32_t m = nseg * NB;
@@ -497,34 +540,81 @@ __global__ void __launch_bounds__(1024) k_plan_small(uint32_t nseg, uint32_t til
       tb.seg_flip[s] = neg;
     }
     __syncthreads();
-    // fold: every block's counts under its segment's class, (segment, packet, block) order
+    // fold + exclusive scan in chunks of kChunk entries: every thread loads and
+    // folds kPer entries strided by the CTA size (coalesced, all loads in flight
+    // at once) into shared memory, then scans kPer contiguous ones (raking),
+    // and the chunk leaves coalesced with the running carry
     const uint32_t total = tb.blk_prefix[nseg];
-    for (uint32_t idx = tid; idx < total * NB; idx += nt) {
-      const uint32_t b = idx / NB, p = idx % NB;
-      const uint32_t s = find_seg(tb.blk_prefix, nseg, b);
-      const uint32_t first = tb.blk_prefix[s], nb_s = tb.blk_prefix[s + 1] - first;
-      const uint32_t C = tb.seg_class[s], cb = tb.cls_raw[b];
-      const uint32_t* raw = tb.cnt_raw + static_cast<size_t>(b) * NB;
-      uint32_t v = 0;
-      if constexpr (NB == 10) {
-        if (cb == C) {
-          v = raw[p];
-        } else if (p == 0) {  // every key of the block is below 10^(C-1): packet 0
+    const uint32_t E = total * NB;
+    const uint32_t C0 = tb.seg_class[0];
+    const uint32_t lane = tid & 31, wid = tid >> 5;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < E; base += kChunk) {
+      uint32_t cb[kPer], direct[kPer], bb[kPer], pp[kPer], cc[kPer];
 #pragma unroll
-          for (int t = 0; t < 10; ++t) v += raw[t];
+      for (int k = 0; k < kPer; ++k) {
+        const uint32_t e = base + k * kPlanThreads + tid;
+        uint32_t b = 0, p = 0, C = C0;
+        if (e < E) {
+          if (nseg == 1) {
+            p = e / total;
+            b = e - p * total;
+          } else {
+            folded_pos<NB>(tb, nseg, e, b, p, C);
+          }
         }
-      } else {
-        const uint32_t d = (C > 8 ? C - 8 : 0) - (cb > 8 ? cb - 8 : 0);
-        const uint32_t lo = p << d, hi = min(static_cast<uint32_t>(NB), (p + 1) << d);
-        for (uint32_t t = lo; t < hi; ++t) v += raw[t];
+        bb[k] = b;
+        pp[k] = p;
+        cc[k] = C;
+        cb[k] = (e < E) ? tb.cls_raw[b] : C;
+        direct[k] = (e < E) ? tb.cnt_raw[static_cast<size_t>(b) * NB + p] : 0u;
       }
-      tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s + (b - first)] = v;
+#pragma unroll
+      for (int k = 0; k < kPer; ++k)
+        s_chunk[chunk_pad(k * kPlanThreads + tid)] =
+            (cb[k] == cc[k]) ? direct[k] : fold_other<NB>(tb, bb[k], pp[k], cb[k], cc[k]);
+      __syncthreads();
+      uint32_t x[kPer];
+      uint32_t sum = 0;
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        x[k] = s_chunk[chunk_pad(tid * kPer + k)];
+        sum += x[k];
+      }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= static_cast<uint32_t>(o)) incl += y;
+      }
+      if (lane == 31) s_warp[wid] = incl;
+      __syncthreads();
+      if (wid == 0) {
+        uint32_t w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+          if (lane >= static_cast<uint32_t>(o)) w += y;
+        }
+        s_warp[lane] = w;  // inclusive over warps
+      }
+      __syncthreads();
+      uint32_t run = carry + incl - sum + (wid ? s_warp[wid - 1] : 0u);
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        s_chunk[chunk_pad(tid * kPer + k)] = run;
+        run += x[k];
+      }
+      const uint32_t chunk_total = s_warp[31];
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const uint32_t e = base + k * kPlanThreads + tid;
+        if (e < E) tb.flat[e] = s_chunk[chunk_pad(k * kPlanThreads + tid)];
+      }
+      carry += chunk_total;
+      __syncthreads();  // s_chunk and s_warp are reused by the next chunk
     }
-    __syncthreads();
-    // absolute first positions
-    uint32_t* grand = tb.scan_part;  // scratch word
-    cta_exclusive_scan(tb.flat, total * NB, grand, s_warp, &s_carry);
-    __syncthreads();
     // packet starts and tiles
     for (uint32_t idx = tid; idx < m; idx += nt) {
       const uint32_t s = idx / NB, p = idx % NB;
@@ -701,8 +791,11 @@ struct ScatterSmallLayout {
   static constexpr size_t bytes = SK + SV + OK + OV + PREF;
 };
 
+// Register budget: four CTAs per SM for 4-byte keys without values (64
+// registers; its shared memory, ~40 KB, fits four times under the largest
+// carveout, which the launch requests), two otherwise.
 template <class K, bool HAS_V, int NB, int BLOCK, int IPT>
-__global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 3) k_scatter_small(const K* __restrict__ keys_in,
+__global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_scatter_small(const K* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
                                                             K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                             uint32_t nseg, uint32_t part_tile, Tables tb) {

@@ -213,3 +213,24 @@ def test_merge_passes_one_by_one(oracle, dist, nb, fan):
             assert_equal(gk, ek, f"{dist} keys after merge pass {r} (fan-in {fan}, values {has_vals})")
             if has_vals:
                 assert_equal(gv, ev, f"{dist} values after merge pass {r} (fan-in {fan})")
+
+
+@pytest.mark.parametrize("case", ["g16_keys", "g4_keys", "g4_pairs"])
+def test_corank_lane_groups(oracle, case):
+    # two-way merge passes at sizes that take each co-rank shape: 16 lanes per
+    # search (at most 4096 merge blocks), 4 lanes (at most 16384), keys and
+    # stable pairs, ten packets and one packet, spread keys and heavy ties
+    n = {"g16_keys": (1 << 22) + 77, "g4_keys": (1 << 25) + 999, "g4_pairs": 16_000_003}[case]
+    has_vals = case.endswith("pairs")
+    dists = ["uniform64", "distinct2p24"] if has_vals else ["uniform31", "distinct16"]
+    for dist in dists:
+        keys = I.generate(dist, n, seed=47)
+        vals = I.index_values(n) if has_vals else None
+        for nb in (10, 1):
+            ek, ev, eoff = oracle.sort(keys, vals, nb)
+            gk, gv, goff, st = run(keys, vals, nb, fan_in=2)
+            assert st == 0
+            assert_equal(goff, eoff, f"{case} {dist} nb={nb} packet offsets")
+            assert_equal(gk, ek, f"{case} {dist} nb={nb} keys")
+            if has_vals:
+                assert_equal(gv, ev, f"{case} {dist} nb={nb} values (stable order)")
