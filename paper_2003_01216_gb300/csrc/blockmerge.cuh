@@ -87,6 +87,46 @@ __device__ __forceinline__ bool merge_geom(const Tables& tb, uint32_t npk, uint3
 }
 
 // ---------------------------------------------------------------------------
+// Search by a group of G lanes (G a power of two, at most 16; lanes
+// [gbase, gbase + G) of the warp, j = this lane's index in the group): the
+// first position in [lo, hi) whose predicate `taken` is false, hi if none,
+// for a predicate that is true on a prefix of the interval.  Every step the
+// G lanes probe G evenly spaced points at once, so the interval shrinks
+// (G + 1)-fold per dependent load instead of 2-fold; once it holds at most G
+// points all of them are probed.  Every lane of the warp calls it (the loop
+// is warp-uniform); a group with an empty interval probes nothing.
+// ---------------------------------------------------------------------------
+template <int G, class Taken>
+__device__ __forceinline__ uint32_t group_search(uint32_t lo, uint32_t hi, int j, int gbase, Taken taken) {
+  static_assert(G >= 2 && G <= 16 && (G & (G - 1)) == 0, "group of 2, 4, 8 or 16 lanes");
+  while (__any_sync(0xffffffffu, lo < hi)) {
+    const uint32_t n = hi - lo;
+    bool t = false;
+    if (n > 0) {
+      const uint32_t m = (n <= static_cast<uint32_t>(G))
+                             ? lo + j
+                             : lo + static_cast<uint32_t>((static_cast<uint64_t>(j + 1) * n) / (G + 1));
+      if (m < hi) t = taken(m);
+    }
+    const uint32_t k = __popc((__ballot_sync(0xffffffffu, t) >> gbase) & ((1u << G) - 1u));
+    if (n > 0) {
+      if (n <= static_cast<uint32_t>(G)) {  // every point of the interval probed
+        lo += k;
+        hi = lo;
+      } else {  // the taken probes are a prefix: keep the gap after the last one
+        const uint32_t nlo = k ? lo + static_cast<uint32_t>((static_cast<uint64_t>(k) * n) / (G + 1)) + 1u : lo;
+        const uint32_t nhi =
+            (k < static_cast<uint32_t>(G)) ? lo + static_cast<uint32_t>((static_cast<uint64_t>(k + 1) * n) / (G + 1))
+                                           : hi;
+        lo = nlo;
+        hi = nhi;
+      }
+    }
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
 // In-register sorting networks over N items.
 // ---------------------------------------------------------------------------
 template <class K>

@@ -179,6 +179,18 @@ hs_status launch_corank(Launcher& lc, K* keys, K* kw, MergeRec* recs, uint32_t n
   return lc.kernel("corank", ck, grid, 256, 0, keys, kw, recs, npk, r, tb);
 }
 
+// Fan-in-4 sample ranking: one warp per sample (eight lanes per run) up to
+// this many tiles, one thread per sample above.
+constexpr size_t kBound4WarpTiles = 1024;
+template <class K, int T, int LG>
+hs_status launch_bound4(Launcher& lc, K* keys, K* kw, Rec4* recs, uint32_t* list, uint32_t npk, int r,
+                        const Tables& tb) {
+  static int grid = 0;
+  auto ck = k_bound4<K, T, kMerge4Spt, LG>;
+  if (!grid) grid = persistent_grid(ck, 256, 0);
+  return lc.kernel("bound4", ck, grid, 256, 0, keys, kw, recs, list, npk, r, tb);
+}
+
 // One sort call.  keys/vals: the caller's arrays (U).  offs: batch offsets
 // (device) or nullptr for one segment.  ws: work space of at least
 // make_layout(...).total bytes.
@@ -286,17 +298,17 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       if (HAS_V) HS_TRY(lc.copy("copy_back_v", vals, vw, n * 4));
     } else if (fan == 4) {
       constexpr int T = sort_tile<K, HAS_V>();
-      static int mgrid = 0, cgrid = 0;
+      static int mgrid = 0;
       const size_t smem = merge4_smem_for<K, HAS_V>();
       auto mk = k_merge4<K, HAS_V, kMerge4Block, kMerge4MinBlocks, merge4_cmax<K, HAS_V>()>;
-      auto ck = k_bound4<K, T, kMerge4Spt>;
       if (!mgrid) mgrid = persistent_grid(mk, kMerge4Block, smem);
-      if (!cgrid) cgrid = persistent_grid(ck, 256, 0);
       Rec4* recs = reinterpret_cast<Rec4*>(ws + L.recs);
       uint32_t* list = reinterpret_cast<uint32_t*>(ws + L.list);
       const int P = o.stop_after >= 3 ? std::min(worst_passes(n, T, 4), o.stop_after - 2) : worst_passes(n, T, 4);
+      const bool warp_per_sample = (n + T - 1) / T <= kBound4WarpTiles;
       for (int r = 1; r <= P; ++r) {
-        HS_TRY(lc.kernel("bound4", ck, cgrid, 256, 0, keys, kw, recs, list, L.npk, r, tb));
+        if (warp_per_sample) HS_TRY((launch_bound4<K, T, 8>(lc, keys, kw, recs, list, L.npk, r, tb)));
+        else HS_TRY((launch_bound4<K, T, 1>(lc, keys, kw, recs, list, L.npk, r, tb)));
         HS_TRY(lc.kernel("merge4", mk, mgrid, kMerge4Block, smem, keys, vals, kw, vw, recs, list, r, tb));
       }
     } else {

@@ -69,14 +69,11 @@ __device__ __forceinline__ void push_recs(bool writer, const MergeRec& rec, Merg
 }
 
 // G == 1: one thread per merge block, its two searches interleaved.
-// G > 1: G lanes per search, 2G lanes per merge block: every step the G lanes
-// probe G evenly spaced points of the remaining interval at once, so the
-// interval shrinks (G + 1)-fold per dependent load instead of 2-fold (few
-// merge blocks: the pass is bound by the latency of the search chain).
+// G > 1: 2G lanes per merge block, G per search (group_search), for passes
+// with few merge blocks, which are bound by the latency of the search chain.
 template <class K, int TILE, int G>
 __global__ void k_corank(const K* __restrict__ ku, const K* __restrict__ kw, MergeRec* __restrict__ recs,
                          uint32_t npk, int r, Tables tb) {
-  static_assert(G == 1 || (G >= 2 && G <= 16 && (G & (G - 1)) == 0), "group of 1, 2, 4, 8 or 16 lanes");
   griddep_open();
   if (static_cast<uint32_t>(r) > tb.pass_ctl[0]) return;  // no packet needs pass r
   const uint32_t total = tb.unit_prefix[npk];
@@ -122,33 +119,9 @@ __global__ void k_corank(const K* __restrict__ ku, const K* __restrict__ kw, Mer
         lo = d > g.b_len ? d - g.b_len : 0u;
         hi = min(d, g.a_len);
       }
-      // invariant: the co-rank lies in [lo, hi]; probe m is "taken" (the
-      // co-rank exceeds m) when B[d - 1 - m] does not precede A[m]
-      while (__any_sync(0xffffffffu, lo < hi)) {
-        const uint32_t n = hi - lo;
-        bool taken = false;
-        if (n > 0) {
-          const uint32_t m = (n <= static_cast<uint32_t>(G))
-                                 ? lo + j
-                                 : lo + static_cast<uint32_t>((static_cast<uint64_t>(j + 1) * n) / (G + 1));
-          if (m < hi) taken = !(B[d - 1 - m] < A[m]);
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, taken);
-        const uint32_t k = __popc((bal >> gbase) & ((1u << G) - 1u));
-        if (n > 0) {
-          if (n <= static_cast<uint32_t>(G)) {  // every point of the interval probed
-            lo += k;
-            hi = lo;
-          } else {  // taken probes are a prefix (the predicate is monotone)
-            const uint32_t nlo = k ? lo + static_cast<uint32_t>((static_cast<uint64_t>(k) * n) / (G + 1)) + 1u : lo;
-            const uint32_t nhi =
-                (k < static_cast<uint32_t>(G)) ? lo + static_cast<uint32_t>((static_cast<uint64_t>(k + 1) * n) / (G + 1))
-                                               : hi;
-            lo = nlo;
-            hi = nhi;
-          }
-        }
-      }
+      // probe m is taken (the co-rank exceeds m) when B[d - 1 - m] does not
+      // precede A[m]
+      lo = group_search<G>(lo, hi, j, gbase, [&](uint32_t m) { return !(B[d - 1 - m] < A[m]); });
       const int l0 = lane - sub;  // lane holding the block's first co-rank
       const uint32_t i0 = __shfl_sync(0xffffffffu, lo, l0);
       const uint32_t i1 = __shfl_sync(0xffffffffu, lo, l0 + G);

@@ -60,7 +60,107 @@ __device__ __forceinline__ uint32_t samples_before(uint32_t x) {
   return x ? (x - 1) / S : 0u;
 }
 
+// Record of the chunk that starts at sample boundary q of a group (every G-th
+// boundary): returns false (and sets kErrBounds) for a slot outside the packet,
+// which the sample bound rules out.
+template <int TILE, int SPT>
+__device__ __forceinline__ bool bound4_record(uint32_t q, uint32_t up0, uint32_t ntiles, uint64_t pstart,
+                                              uint64_t g0, uint64_t R, bool srcw, const uint32_t (&c)[4],
+                                              const uint32_t (&lens)[4], Rec4* recs, uint32_t* err,
+                                              uint32_t& u_out) {
+  constexpr int G = kSamplesPerChunk;
+  constexpr uint32_t S = sample_gap<TILE, SPT>();
+  uint32_t nbound = 1;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) nbound += samples_before<S>(lens[j]);
+  const uint32_t chunk = q / G, chunks = (nbound + G - 1) / G;
+  u_out = (up0 + static_cast<uint32_t>(g0 / TILE)) * SPT + chunk;
+  if (chunk >= chunks || u_out >= (up0 + ntiles) * SPT) {  // cannot happen; never write out of the packet
+    atomicOr(err, kErrBounds);
+    return false;
+  }
+  Rec4 rec;
+  rec.base = (pstart + g0) | (srcw ? kSrcW : 0ull);
+  rec.run = static_cast<uint32_t>(R);
+  rec.last = (chunk + 1 == chunks) ? 1u : 0u;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    rec.c[j] = c[j];
+    rec.len[j] = lens[j];
+  }
+  recs[u_out] = rec;
+  return true;
+}
+
+// k_bound4 with one warp per sample slot: lanes 8j .. 8j+7 find the sample's
+// rank in run j together (the sample's own run is skipped); lane 0 writes the
+// chunk record and lists it.
 template <class K, int TILE, int SPT>
+__device__ __forceinline__ void bound4_warp(const K* __restrict__ ku, const K* __restrict__ kw,
+                                            Rec4* __restrict__ recs, uint32_t* __restrict__ list, uint32_t npk,
+                                            int r, const Tables& tb, uint32_t total, int lane) {
+  constexpr int G = kSamplesPerChunk;
+  constexpr uint32_t S = sample_gap<TILE, SPT>();
+  constexpr uint32_t PER_TILE = SPT * G;
+  const int jr = lane >> 3, t = lane & 7;  // run searched by this lane, lane in its group
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t z = warp; z < total; z += nwarps) {  // warp-uniform: one sample slot per warp
+    const uint32_t u = z / PER_TILE, sub = z % PER_TILE;
+    const uint32_t p = find_pkt(tb.unit_prefix, npk, u);
+    const uint32_t up0 = tb.unit_prefix[p], ntiles = tb.unit_prefix[p + 1] - up0;
+    const int passes = passes_of(ntiles, 2);
+    const uint64_t pstart = tb.pkt_off[p], len = tb.pkt_off[p + 1] - pstart;
+    const uint64_t k = static_cast<uint64_t>(u - up0) * TILE + static_cast<uint64_t>(sub) * S;
+    if (!(r <= passes && k < len)) continue;
+    const uint64_t R = static_cast<uint64_t>(TILE) << (2 * (r - 1));
+    const uint64_t g0 = k - k % (4 * R);
+    const uint32_t i = static_cast<uint32_t>((k - g0) / R);
+    const uint32_t pos = static_cast<uint32_t>((k - g0) % R);
+    if (pos == 0 && i != 0) continue;  // neither a sample nor the group start
+    uint32_t lens[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t st = g0 + static_cast<uint64_t>(j) * R;
+      lens[j] = st >= len ? 0u : static_cast<uint32_t>(min(R, len - st));
+    }
+    const bool srcw = ((passes - r + 1) & 1) != 0;  // the buffer holding pass r-1
+    const K* gb = (srcw ? kw : ku) + pstart + g0;
+    uint32_t c[4] = {0, 0, 0, 0};
+    uint32_t q = 0;
+    if (pos != 0) {
+      const K e = gb[static_cast<uint64_t>(i) * R + pos];
+      const K* run = gb + static_cast<uint64_t>(jr) * R;
+      const bool earlier = static_cast<uint32_t>(jr) < i;
+      // items of run jr that come before e in the merged order
+      uint32_t len_jr = lens[0];  // lens[jr] without a dynamically indexed array
+#pragma unroll
+      for (int j = 1; j < 4; ++j) len_jr = (jr == j) ? lens[j] : len_jr;
+      const uint32_t hi = (static_cast<uint32_t>(jr) == i) ? 0u : len_jr;
+      const uint32_t rank = group_search<8>(0u, hi, t, lane & ~7, [&](uint32_t m) {
+        const K x = run[m];
+        return earlier ? !(e < x) : (x < e);
+      });
+      q = pos / S;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t rj = __shfl_sync(0xffffffffu, rank, 8 * j);
+        c[j] = (static_cast<uint32_t>(j) == i) ? pos : rj;
+        if (static_cast<uint32_t>(j) != i) q += samples_before<S>(c[j]);
+      }
+    }
+    if (lane == 0 && q % G == 0) {
+      uint32_t u_out = 0;
+      if (bound4_record<TILE, SPT>(q, up0, ntiles, pstart, g0, R, srcw, c, lens, recs, tb.err, u_out))
+        list[atomicAdd(&tb.pass_ctl[r], 1u)] = u_out;
+    }
+  }
+}
+
+// LG == 1: one thread per sample slot, its three searches interleaved.
+// LG == 8: one warp per sample slot, eight lanes per run (group_search), for
+// passes with few samples, which are bound by the latency of the search chain.
+template <class K, int TILE, int SPT, int LG>
 __global__ void k_bound4(const K* __restrict__ ku, const K* __restrict__ kw, Rec4* __restrict__ recs,
                          uint32_t* __restrict__ list, uint32_t npk, int r, Tables tb) {
   griddep_open();
@@ -68,9 +168,14 @@ __global__ void k_bound4(const K* __restrict__ ku, const K* __restrict__ kw, Rec
   constexpr uint32_t S = sample_gap<TILE, SPT>();
   constexpr uint32_t PER_TILE = SPT * G;  // sample slots per tile
   static_assert(S * PER_TILE == TILE, "whole chunk slots per tile");
+  static_assert(LG == 1 || LG == 8, "a thread or a warp per sample");
   if (static_cast<uint32_t>(r) > tb.pass_ctl[0]) return;  // no packet needs pass r
   const uint32_t total = tb.unit_prefix[npk] * PER_TILE;
   const int lane = threadIdx.x & 31;
+  if constexpr (LG == 8) {
+    bound4_warp<K, TILE, SPT>(ku, kw, recs, list, npk, r, tb, total, lane);
+    return;
+  }
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
     const uint32_t z = base + lane;
@@ -135,28 +240,8 @@ __global__ void k_bound4(const K* __restrict__ ku, const K* __restrict__ kw, Rec
               if (static_cast<uint32_t>(j) != i) q += samples_before<S>(c[j]);
             }
           }
-          if (q % G == 0) {
-            uint32_t nbound = 1;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) nbound += samples_before<S>(lens[j]);
-            const uint32_t chunk = q / G, chunks = (nbound + G - 1) / G;
-            u_out = (up0 + static_cast<uint32_t>(g0 / TILE)) * SPT + chunk;
-            if (chunk >= chunks || u_out >= (up0 + ntiles) * SPT) {  // cannot happen; never write out of the packet
-              atomicOr(tb.err, kErrBounds);
-            } else {
-              Rec4 rec;
-              rec.base = (pstart + g0) | (srcw ? kSrcW : 0ull);
-              rec.run = static_cast<uint32_t>(R);
-              rec.last = (chunk + 1 == chunks) ? 1u : 0u;
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                rec.c[j] = c[j];
-                rec.len[j] = lens[j];
-              }
-              recs[u_out] = rec;
-              active = true;
-            }
-          }
+          if (q % G == 0)
+            active = bound4_record<TILE, SPT>(q, up0, ntiles, pstart, g0, R, srcw, c, lens, recs, tb.err, u_out);
         }
       }
     }
