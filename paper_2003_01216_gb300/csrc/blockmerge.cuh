@@ -7,7 +7,9 @@
 //               sequential quicksort of one data part.
 //   k_corank    merge pass r, for every merge block (TILE outputs) the split of
 //               its first and one-past-last output between the two runs it
-//               merges (merge path: binary search along the cross diagonal).
+//               merges (merge path: a search along the cross diagonal, binary
+//               per thread, or by a group of lanes when the pass has few
+//               merge blocks).
 //   k_merge     merge pass r: one CTA writes TILE consecutive outputs of one
 //               pair of runs of length TILE * 2^(r-1); runs never cross a packet
 //               boundary.  Passes repeat until every packet is one run: the
