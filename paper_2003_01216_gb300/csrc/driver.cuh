@@ -160,6 +160,13 @@ inline size_t merge_smem() {  // two input stages (+ two output buffers when the
   return merge_buffers<K, HAS_V, T>() * merge_stage_bytes<K, HAS_V>(T);
 }
 
+// A persistent grid never larger than the work a call can have (every
+// persistent kernel loops over its work, so any grid size is correct; CTAs
+// that would find nothing to do are not launched).
+inline int capped(int grid, uint64_t need) {
+  return static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(static_cast<uint64_t>(grid), need)));
+}
+
 template <class Kern>
 inline int persistent_grid(Kern kern, int block, size_t smem) {
   int dev = 0, sms = 0, occ = 0;
@@ -172,11 +179,13 @@ inline int persistent_grid(Kern kern, int block, size_t smem) {
 }
 
 template <class K, int T, int G>
-hs_status launch_corank(Launcher& lc, K* keys, K* kw, MergeRec* recs, uint32_t npk, int r, const Tables& tb) {
+hs_status launch_corank(Launcher& lc, K* keys, K* kw, MergeRec* recs, uint32_t npk, int r, const Tables& tb,
+                        uint64_t max_units) {
   static int grid = 0;
   auto ck = k_corank<K, T, G>;
   if (!grid) grid = persistent_grid(ck, 256, 0);
-  return lc.kernel("corank", ck, grid, 256, 0, keys, kw, recs, npk, r, tb);
+  const uint64_t lanes = max_units * (G == 1 ? 1 : 2 * G);  // lanes per merge block
+  return lc.kernel("corank", ck, capped(grid, (lanes + 255) / 256), 256, 0, keys, kw, recs, npk, r, tb);
 }
 
 // Fan-in-4 sample ranking: one warp per sample (eight lanes per run) up to
@@ -184,11 +193,12 @@ hs_status launch_corank(Launcher& lc, K* keys, K* kw, MergeRec* recs, uint32_t n
 constexpr size_t kBound4WarpTiles = 1024;
 template <class K, int T, int LG>
 hs_status launch_bound4(Launcher& lc, K* keys, K* kw, Rec4* recs, uint32_t* list, uint32_t npk, int r,
-                        const Tables& tb) {
+                        const Tables& tb, uint64_t max_units) {
   static int grid = 0;
   auto ck = k_bound4<K, T, kMerge4Spt, LG>;
   if (!grid) grid = persistent_grid(ck, 256, 0);
-  return lc.kernel("bound4", ck, grid, 256, 0, keys, kw, recs, list, npk, r, tb);
+  const uint64_t lanes = max_units * kMerge4Spt * kSamplesPerChunk * (LG == 1 ? 1 : 32);  // per sample slot
+  return lc.kernel("bound4", ck, capped(grid, (lanes + 255) / 256), 256, 0, keys, kw, recs, list, npk, r, tb);
 }
 
 // One sort call.  keys/vals: the caller's arrays (U).  offs: batch offsets
@@ -228,7 +238,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       auto kern = k_hist<K, NB, kBlock, kIpt>;
       if (!grid) grid = persistent_grid(kern, kBlock, smem);
       for (int img = 0; img < (std::is_same<K, int32_t>::value ? 2 : 1); ++img) {
-        HS_TRY(lc.kernel(img ? "hist_flip" : "hist", kern, grid, kBlock, smem, keys, nseg32, kTile, img, tb));
+        HS_TRY(lc.kernel(img ? "hist_flip" : "hist", kern, capped(grid, L.max_blocks), kBlock, smem, keys, nseg32, kTile,
+                         img, tb));
       }
     }
     if (small) {
@@ -263,7 +274,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         grid = persistent_grid(kern, kBlock, smem);
       }
-      HS_TRY(lc.kernel("scatter", kern, grid, kBlock, smem, keys, vals, kw, vw, nseg32, kTile, tb));
+      HS_TRY(lc.kernel("scatter", kern, capped(grid, L.max_blocks), kBlock, smem, keys, vals, kw, vw, nseg32, kTile,
+                       tb));
     } else {
       const size_t smem = scatter_smem<K, HAS_V, NB>();
       auto kern = k_scatter<K, HAS_V, NB, kBlock, kIpt>;
@@ -290,7 +302,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       const uint64_t limit_ns = stuck ? 2000000ull : 2000000000ull;  // 2 ms when injected, else 2 s
       const K* ts_k = (NB == 1) ? keys : kw;
       const uint32_t* ts_v = (NB == 1) ? vals : vw;
-      HS_TRY(lc.kernel("tilesort", kern, grid, kBlock, smem, ts_k, ts_v, keys, vals, kw, vw, L.npk,
+      HS_TRY(lc.kernel("tilesort", kern, capped(grid, L.max_units), kBlock, smem, ts_k, ts_v, keys, vals, kw, vw, L.npk,
                        o.stop_after == 2 ? 1 : 0, stuck ? 1 : 0, limit_ns, tb));
     }
     if (o.stop_after == 2) {
@@ -307,9 +319,10 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       const int P = o.stop_after >= 3 ? std::min(worst_passes(n, T, 4), o.stop_after - 2) : worst_passes(n, T, 4);
       const bool warp_per_sample = (n + T - 1) / T <= kBound4WarpTiles;
       for (int r = 1; r <= P; ++r) {
-        if (warp_per_sample) HS_TRY((launch_bound4<K, T, 8>(lc, keys, kw, recs, list, L.npk, r, tb)));
-        else HS_TRY((launch_bound4<K, T, 1>(lc, keys, kw, recs, list, L.npk, r, tb)));
-        HS_TRY(lc.kernel("merge4", mk, mgrid, kMerge4Block, smem, keys, vals, kw, vw, recs, list, r, tb));
+        if (warp_per_sample) HS_TRY((launch_bound4<K, T, 8>(lc, keys, kw, recs, list, L.npk, r, tb, L.max_units)));
+        else HS_TRY((launch_bound4<K, T, 1>(lc, keys, kw, recs, list, L.npk, r, tb, L.max_units)));
+        HS_TRY(lc.kernel("merge4", mk, capped(mgrid, static_cast<uint64_t>(L.max_units) * kMerge4Spt), kMerge4Block,
+                         smem, keys, vals, kw, vw, recs, list, r, tb));
       }
     } else {
       static int mgrid = 0;
@@ -321,10 +334,10 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       const int P = o.stop_after >= 3 ? std::min(worst_passes(n, T), o.stop_after - 2) : worst_passes(n, T);
       const int G = corank_group((n + T - 1) / T);
       for (int r = 1; r <= P; ++r) {
-        if (G == 16) HS_TRY((launch_corank<K, T, 16>(lc, keys, kw, recs, L.npk, r, tb)));
-        else if (G == 4) HS_TRY((launch_corank<K, T, 4>(lc, keys, kw, recs, L.npk, r, tb)));
-        else HS_TRY((launch_corank<K, T, 1>(lc, keys, kw, recs, L.npk, r, tb)));
-        HS_TRY(lc.kernel("merge", mk, mgrid, kBlock, smem, keys, vals, kw, vw, recs, r, tb));
+        if (G == 16) HS_TRY((launch_corank<K, T, 16>(lc, keys, kw, recs, L.npk, r, tb, L.max_units)));
+        else if (G == 4) HS_TRY((launch_corank<K, T, 4>(lc, keys, kw, recs, L.npk, r, tb, L.max_units)));
+        else HS_TRY((launch_corank<K, T, 1>(lc, keys, kw, recs, L.npk, r, tb, L.max_units)));
+        HS_TRY(lc.kernel("merge", mk, capped(mgrid, L.max_units), kBlock, smem, keys, vals, kw, vw, recs, r, tb));
       }
     }
     if (o.stop_after >= 3) {  // testing: the state after merge pass r, gathered into the caller's array
