@@ -160,6 +160,20 @@ inline size_t merge_smem() {  // two input stages (+ two output buffers when the
   return merge_buffers<K, HAS_V, T>() * merge_stage_bytes<K, HAS_V>(T);
 }
 
+// Launch shapes are cached per device: kernel attributes (shared-memory size,
+// carveout) are set per device, and the occupancy query is per device.
+constexpr int kMaxDevices = 64;
+struct PerDevice {
+  int v[kMaxDevices] = {};
+  int& operator()() {
+    int d = 0;
+    cudaGetDevice(&d);
+    static int spare;  // devices beyond the table: recomputed on every call
+    if (d < 0 || d >= kMaxDevices) return spare = 0;
+    return v[d];
+  }
+};
+
 // A persistent grid never larger than the work a call can have (every
 // persistent kernel loops over its work, so any grid size is correct; CTAs
 // that would find nothing to do are not launched).
@@ -181,7 +195,8 @@ inline int persistent_grid(Kern kern, int block, size_t smem) {
 template <class K, int T, int G>
 hs_status launch_corank(Launcher& lc, K* keys, K* kw, MergeRec* recs, uint32_t npk, int r, const Tables& tb,
                         uint64_t max_units) {
-  static int grid = 0;
+  static PerDevice grid_cache;
+  int& grid = grid_cache();
   auto ck = k_corank<K, T, G>;
   if (!grid) grid = persistent_grid(ck, 256, 0);
   const uint64_t lanes = max_units * (G == 1 ? 1 : 2 * G);  // lanes per merge block
@@ -194,7 +209,8 @@ constexpr size_t kBound4WarpTiles = 1024;
 template <class K, int T, int LG>
 hs_status launch_bound4(Launcher& lc, K* keys, K* kw, Rec4* recs, uint32_t* list, uint32_t npk, int r,
                         const Tables& tb, uint64_t max_units) {
-  static int grid = 0;
+  static PerDevice grid_cache;
+  int& grid = grid_cache();
   auto ck = k_bound4<K, T, kMerge4Spt, LG>;
   if (!grid) grid = persistent_grid(ck, 256, 0);
   const uint64_t lanes = max_units * kMerge4Spt * kSamplesPerChunk * (LG == 1 ? 1 : 32);  // per sample slot
@@ -233,7 +249,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     }
   } else {
     {
-      static int grid = 0;
+      static PerDevice grid_cache;
+      int& grid = grid_cache();
       const size_t smem = hist_smem<K>();
       auto kern = k_hist<K, NB, kBlock, kIpt>;
       if (!grid) grid = persistent_grid(kern, kBlock, smem);
@@ -247,7 +264,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     } else {
     HS_TRY(lc.kernel("finalize", (k_finalize<NB>), (nseg32 + 255) / 256, 256, 0, nseg32, tb));
     {
-      static int grid = 0;
+      static PerDevice grid_cache;
+      int& grid = grid_cache();
       if (!grid) grid = persistent_grid(k_fold<NB>, 256, 0);
       HS_TRY(lc.kernel("fold", (k_fold<NB>), grid, 256, 0, nseg32, tb));
     }
@@ -258,7 +276,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     HS_TRY(lc.kernel("scan_partials", k_scan_partials, 1, kScanBlock, 0, tb.scan_part));
     HS_TRY(lc.kernel("scan_down", k_scan_down, kScanChunks, kScanBlock, 0, tb.flat, m_ptr, NB, tb.scan_part));
     {
-      static int grid = 0;
+      static PerDevice grid_cache;
+      int& grid = grid_cache();
       if (!grid) grid = persistent_grid(k_pkt<NB>, 256, 0);
       HS_TRY(lc.kernel("pkt", (k_pkt<NB>), grid, 256, 0, nseg32, sort_tile<K, HAS_V>(), tb));
     }
@@ -267,7 +286,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
 
     if constexpr (NB <= 16) {
       // persistent: bulk copies in and out, ranks from one scan of packed counts
-      static int grid = 0;
+      static PerDevice grid_cache;
+      int& grid = grid_cache();
       const size_t smem = ScatterSmallLayout<K, HAS_V, kBlock, kIpt>::bytes;
       auto kern = k_scatter_small<K, HAS_V, NB, kBlock, kIpt>;
       if (!grid) {
@@ -279,10 +299,11 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     } else {
       const size_t smem = scatter_smem<K, HAS_V, NB>();
       auto kern = k_scatter<K, HAS_V, NB, kBlock, kIpt>;
-      static bool attr = false;
+      static PerDevice attr_cache;
+      int& attr = attr_cache();
       if (!attr) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        attr = true;
+        attr = 1;
       }
       HS_TRY(lc.kernel("scatter", kern, L.max_blocks, kBlock, smem, keys, vals, kw, vw, nseg32, kTile, tb));
     }
@@ -294,7 +315,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     }
   } else {
     {
-      static int grid = 0;
+      static PerDevice grid_cache;
+      int& grid = grid_cache();
       const size_t smem = sort_smem<K, HAS_V>();
       auto kern = k_tilesort<K, HAS_V, kBlock, sort_ipt<K, HAS_V>()>;
       if (!grid) grid = persistent_grid(kern, kBlock, smem);
@@ -310,7 +332,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       if (HAS_V) HS_TRY(lc.copy("copy_back_v", vals, vw, n * 4));
     } else if (fan == 4) {
       constexpr int T = sort_tile<K, HAS_V>();
-      static int mgrid = 0;
+      static PerDevice mgrid_cache;
+      int& mgrid = mgrid_cache();
       const size_t smem = merge4_smem_for<K, HAS_V>();
       auto mk = k_merge4<K, HAS_V, kMerge4Block, kMerge4MinBlocks, merge4_cmax<K, HAS_V>()>;
       if (!mgrid) mgrid = persistent_grid(mk, kMerge4Block, smem);
@@ -325,7 +348,8 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
                          smem, keys, vals, kw, vw, recs, list, r, tb));
       }
     } else {
-      static int mgrid = 0;
+      static PerDevice mgrid_cache;
+      int& mgrid = mgrid_cache();
       const size_t smem = merge_smem<K, HAS_V>();
       auto mk = k_merge<K, HAS_V, kBlock, sort_ipt<K, HAS_V>()>;
       constexpr int T = sort_tile<K, HAS_V>();
