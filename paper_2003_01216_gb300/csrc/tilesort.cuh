@@ -8,6 +8,15 @@ namespace hs {
 // ---------------------------------------------------------------------------
 // k_tilesort
 // ---------------------------------------------------------------------------
+// Merge levels a tile of cnt keys needs: runs of IPT << lv items are merged
+// while the first run does not yet hold every real key.
+template <int IPT, int TILE>
+__device__ __forceinline__ int levels_for(int cnt) {
+  int lv = 0;
+  while ((IPT << lv) < TILE && (IPT << lv) < cnt) ++lv;
+  return lv;
+}
+
 template <class K, bool HAS_V, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, const uint32_t* __restrict__ vw, K* ku,
                                                      uint32_t* vu, K* kw_out, uint32_t* vw_out, uint32_t npk,
@@ -78,9 +87,12 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
     else network_sort<IPT>(k);
 
     // merge levels: runs of `run` = IPT << lv items -> 2 * run, in the region
-    // at offset 0; a pair of runs is merged by 2 << lv threads, IPT outputs each
+    // at offset 0; a pair of runs is merged by 2 << lv threads, IPT outputs each.
+    // Once the first run holds all cnt real keys the tile is sorted (the rest
+    // is padding), so a short tile (the last of a small packet) stops early.
+    const int nlv = levels_for<IPT, TILE>(cnt);
 #pragma unroll 1
-    for (int lv = 0; (IPT << lv) < TILE; ++lv) {
+    for (int lv = 0; lv < nlv; ++lv) {
       const int run = IPT << lv;
       __syncthreads();
 #pragma unroll
