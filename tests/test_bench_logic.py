@@ -1,0 +1,78 @@
+"""The benchmark's host-side logic on the CPU: the byte model of the merge
+passes, the clock samples it keeps, and the traffic record it scales."""
+import datetime
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_merge_active_keys_two_way():
+    # packets of 3 tiles, empty, 2 tiles (one key over), 1 short tile:
+    # passes ceil(log2(tiles)) = 2, 0, 1, 0
+    t = 7936
+    lens = [3 * t, 0, t + 1, 5]
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint64)
+    assert bench.merge_active_keys(off, t, 2) == [3 * t + t + 1, 3 * t]
+
+
+def test_merge_active_keys_four_way():
+    # ceil(log4(tiles)): 17 tiles -> 3 passes, 4 tiles -> 1, 5 tiles -> 2, 1 tile -> 0
+    t = 3840
+    lens = [17 * t, 4 * t, 4 * t + 1, t]
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint64)
+    assert bench.merge_active_keys(off, t, 4) == [17 * t + 4 * t + 4 * t + 1, 17 * t + 4 * t + 1, 17 * t]
+
+
+def test_merge_active_keys_nothing_to_merge():
+    off = np.array([0, 10, 10, 20], dtype=np.uint64)
+    assert bench.merge_active_keys(off, 7936, 2) == []
+
+
+def _write_samples(path, t0, rows):
+    with open(path, "w") as f:
+        for dt, mhz, cap in rows:
+            ts = datetime.datetime.fromtimestamp(t0 + dt).strftime("%Y/%m/%d %H:%M:%S.%f")
+            f.write(f"{ts}, 0, {mhz}, 2070, 610.5, 0x0, Not Active, Not Active, Not Active, "
+                    f"{'Active' if cap else 'Not Active'}\n")
+
+
+def test_clock_summary_keeps_samples_inside_the_region():
+    c = bench.ClockSampler(0)
+    c.proc = object()  # a sampler that "ran"
+    t0 = time.time()
+    # samples 0.1 s before, inside, and after the region [t0, t0 + 0.1]
+    _write_samples(c.path, t0, [(-0.1, 900, False), (0.02, 2070, False), (0.06, 2040, True), (0.5, 1000, False)])
+    try:
+        c.t0, c.t1 = t0, t0 + 0.1
+        s = c.summary()
+        assert s["samples"] == 2 and s["samples_where"] == "inside the timed region"
+        assert s["sm_mhz"] == (2070 + 2040) / 2 and s["reasons"] == ["sw_power_cap"]
+        # a region between samples: the two nearest are kept and said to be so
+        c.t0, c.t1 = t0 + 0.2, t0 + 0.21
+        s = c.summary()
+        assert s["samples"] == 2 and s["samples_where"].startswith("nearest")
+    finally:
+        os.remove(c.path)
+
+
+def test_clock_summary_without_nvidia_smi():
+    c = bench.ClockSampler(0)
+    assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_traffic_record_scales_and_expires():
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+        rec = json.load(f)["merge"]
+    got = bench.ncu_traffic("merge", 1000.0)
+    if rec["source_sha"] == bench.source_sha(*rec["sources"]):
+        assert got == rec["dram_bytes_per_key"] * 1000.0
+    else:  # sources changed since the capture: no traffic figure
+        assert got is None
+    assert bench.ncu_traffic("no_such_kernel", 1000.0) is None
