@@ -39,6 +39,9 @@ WORKLOADS = {
 BATCH_SEGMENTS, BATCH_LO, BATCH_HI = 10_000, 16, 1 << 20
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal bandwidth, for context beside the measured peak
+
+
 def load_peaks() -> tuple[float, str]:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -207,6 +210,25 @@ def ncu_traffic(kernel: str, keys_per_launch: float):
     return rec["dram_bytes_per_key"] * keys_per_launch
 
 
+def per_kernel_roofline(per_kernel: dict, steps: int, key_read: int, sn: int, merge_keys: int, s: int, mk: str,
+                        peak: float) -> dict:
+    """Achieved GB/s of each HBM pass of the sort: its algorithmic bytes per
+    step (hist reads the keys once; scatter and tile sort read and write every
+    element; the merge passes read and write their active keys) over its event
+    time per step, as a fraction of the measured and of the nominal peak."""
+    bytes_of = {"hist": key_read, "scatter": 2 * sn, "tilesort": 2 * sn, mk: 2 * s * merge_keys}
+    out = {}
+    for name, b in bytes_of.items():
+        launches, ms = per_kernel.get(name, (0, 0.0))
+        if ms <= 0:
+            continue
+        ms_step = ms / steps
+        gbs = b / (ms_step / 1e3) / 1e9
+        out[name] = {"bytes_per_step": b, "ms_per_step": ms_step, "achieved_gbs": gbs, "frac": gbs / peak,
+                     "frac_vs_nominal": gbs / NOMINAL_HBM_GBS, "launches_per_step": launches / steps}
+    return out
+
+
 # --------------------------------------------------------------------------
 # reference arm and CPU baseline: the oracle on host cores
 # --------------------------------------------------------------------------
@@ -251,7 +273,7 @@ def run_reference(args, rank, world):
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64" if dist in ("uniform64", "distinct2p24") else "int32", "data": "synthetic",
         "impl": "reference",
-        "config": workload_config(args, dist, n, has_vals),
+        "config": workload_config(args, dist, n, has_vals, world),
         "cpu_baseline": {"value": rate, "unit": "keys/s", "cores": 1, "kind": "oracle",
                          "sample": f"{sample} keys of the workload's distribution per step (the full workload is {n})"},
         "e2e": {"value": rate, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -259,7 +281,8 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(args, dist, n, has_vals):
+def workload_config(args, dist, n, has_vals, world=1):
+    """The workload both arms report (same keys in the GPU and the reference line)."""
     import paper_2003_01216_gb300 as hs
     code = 2 if dist in ("uniform64", "distinct2p24") else 0
     pl = hs.plan(code, n, has_vals, fan_in=args.fan_in)
@@ -267,7 +290,7 @@ def workload_config(args, dist, n, has_vals):
     return {"workload": f"{args.workload}_{n}_{dist}_{args.partition}pkt", "n": n, "dist": dist,
             "key_dtype": "uint64" if dist in ("uniform64", "distinct2p24") else "int32",
             "values": "uint32 input index" if has_vals else None, "partition": args.partition,
-            "tile": tile, "fan_in": fan, "seed": 0,
+            "tile": tile, "fan_in": fan, "seed": 0, "parallelism": f"replicas{world}",
             "l2": "inputs larger than L2 (>= 1 GiB vs 129 MB); a 1 GiB restore copy between timed steps"}
 
 
@@ -293,6 +316,9 @@ def main():
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: requests per second")
     ap.add_argument("--no-serial", action="store_true", help="serve: skip the serial baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="plain: skip the short batch and serve summaries added to the line")
+    ap.add_argument("--extras-serve-s", type=float, default=5.0, help="plain: seconds of arrivals in the serve summary")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if world != args.gpus:
@@ -414,6 +440,7 @@ def main():
     b_alg = s * n * 1 + 2 * s * n + 2 * s * n + 2 * s * sum(active)  # hist + scatter + tile sort + merges
     whole_gbs = b_alg / (mean_ms / 1e3) / 1e9
     floor_gbs = 2 * s * n / (mean_ms / 1e3) / 1e9
+    per_pass = per_kernel_roofline(per_kernel, split_steps, key_bytes * n, s * n, sum(active), s, mk, peak)
 
     # end-to-end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -441,6 +468,15 @@ def main():
         cpu = {"value": rate, "unit": "keys/s", "cores": 1, "kind": "oracle",
                "sample": f"one oracle sort of {sample} keys of the same distribution ({sec:.1f} s)"}
 
+    # configs 4 and 5 in brief, outside the timed region (one GPU only)
+    extras = {}
+    if world == 1 and not args.no_extras and args.workload == "plain":
+        extras["batch"] = {
+            "capped_2^17": batch_measure(dev, 1 << 17, steps=5, warmup=3),
+            "full_2^20": batch_measure(dev, BATCH_HI, steps=3, warmup=3),
+        }
+        extras["serve"] = serve_measure(dev, args.rate, args.extras_serve_s, serial_too=True)
+
     if rank == 0:
         dominant = max(per_kernel.items(), key=lambda kv: kv[1][1])[0] if per_kernel else None
         line = {
@@ -448,15 +484,21 @@ def main():
             "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": max_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32" if key_bytes == 4 else "u64", "data": "synthetic",
-            "config": dict(workload_config(args, dist_name, n, has_vals), merge_passes=len(active),
-                           parallelism=f"replicas{world}"),
+            "config": workload_config(args, dist_name, n, has_vals, world),
             "roofline": {"bound": "hbm", "kernel": mk, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "peak_kind": peak_kind,
+                         "frac_vs_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
+                         "nominal_peak": NOMINAL_HBM_GBS,
                          "algorithmic_bytes_per_launch": merge_bytes / max(1, merge_launches),
                          "avg_launch_ms": merge_ms / max(1, merge_launches)},
             "whole_sort": {"b_alg_bytes": b_alg, "achieved_gbs": whole_gbs, "frac": whole_gbs / peak,
-                           "floor_frac": floor_gbs / peak},
+                           "floor_frac": floor_gbs / peak, "frac_vs_nominal": whole_gbs / NOMINAL_HBM_GBS,
+                           "floor_frac_vs_nominal": floor_gbs / NOMINAL_HBM_GBS,
+                           "merge_passes": len(active), "tile": plan["tile"], "fan_in": plan["fan_in"]},
+            "per_kernel_roofline": per_pass,
+            "batch": extras.get("batch"),
+            "serve": extras.get("serve"),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -473,33 +515,36 @@ def main():
         dist.destroy_process_group()
 
 
-def run_batch(args, rank, world, dev, dist_name):
-    """Batched sort (one CUDA-graph launch for all segments) against the plain
-    sort looped over the segments, same stream, same data."""
+def batch_measure(dev, hi: int, steps: int, warmup: int, dist_name: str = "uniform31", world: int = 1) -> dict:
+    """Config 4: 10,000 int32 segments, lengths log-uniform in [16, hi], sorted
+    by one hs_sort_batch call (one CUDA-graph launch), against the plain sort
+    looped over the segments on the same stream and data.  Returns the timing
+    record (events on the launching stream; the pristine copy before each step
+    is outside the events)."""
     import torch
 
     import paper_2003_01216_gb300 as hs
     from paper_2003_01216_gb300 import inputs as I
 
-    off_h = I.batch_offsets(BATCH_SEGMENTS, BATCH_LO, args.batch_hi, seed=0)
+    off_h = I.batch_offsets(BATCH_SEGMENTS, BATCH_LO, hi, seed=0)
     n = int(off_h[-1])
     offs = torch.from_numpy(off_h).to(dev)
     pristine = I.device_generate(dist_name, n, seed=0)
     work = torch.empty_like(pristine)
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             work.copy_(pristine)
             hs.sort_batch(work, offs, graph=True)
         if hs.stream_error(st) != 0:
             raise RuntimeError("device error during warm-up")
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         with ClockSampler(dev.index) as clk:
             barrier(world, dev)
             torch.cuda.synchronize()
             l0 = hs.kernel_launches()
             clk.mark()
-            for i in range(args.steps):
+            for i in range(steps):
                 work.copy_(pristine)
                 ev[i][0].record(st)
                 hs.sort_batch(work, offs, graph=True)
@@ -509,6 +554,14 @@ def run_batch(args, rank, world, dev, dist_name):
             launches = hs.kernel_launches() - l0
         ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
         ok = hs.stream_error(st) == 0
+        # every segment sorted (device-side property check of the last step)
+        lo_t, hi_t = offs[:-1], offs[1:]
+        d = work[1:] >= work[:-1]
+        inner = torch.ones_like(d)
+        starts = lo_t[(lo_t > 0) & (lo_t < n)].long() - 1  # pairs that straddle a segment start
+        inner[starts] = False
+        sorted_ok = bool((d | ~inner).all().item())
+        del hi_t
         # the same segments through the plain per-array call, looped on one stream
         work.copy_(pristine)
         lo_ = [int(x) for x in off_h]
@@ -521,56 +574,76 @@ def run_batch(args, rank, world, dev, dist_name):
         torch.cuda.synchronize()
         loop_ms = a.elapsed_time(b)
     ms_max = reduce_max(ms, world, dev)
-    value = world * n / (ms_max / 1e3)
+    return {"n": n, "segments": BATCH_SEGMENTS, "lengths": f"log-uniform [{BATCH_LO}, {hi}]",
+            "value": world * n / (ms_max / 1e3), "unit": "keys/s", "ms_per_step": ms_max, "steps": steps,
+            "looped_plain": {"value": n / (loop_ms / 1e3), "unit": "keys/s", "ms": loop_ms,
+                             "calls": BATCH_SEGMENTS},
+            "speedup_vs_looped": loop_ms / ms_max, "gpu_launches": launches, "clocks": clk.summary(),
+            "device_ok": ok, "segments_sorted": sorted_ok}
+
+
+def run_batch(args, rank, world, dev, dist_name):
+    """Batched sort (one CUDA-graph launch for all segments) against the plain
+    sort looped over the segments, same stream, same data."""
+    rec = batch_measure(dev, args.batch_hi, args.steps, args.warmup, dist_name, world)
     if rank == 0:
         print(json.dumps({
             "metric": "batched sort throughput (keys/s): one graph launch over all segments",
-            "value": value, "unit": "keys/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "value": rec["value"], "unit": "keys/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"batch_{BATCH_SEGMENTS}x[{BATCH_LO},{args.batch_hi}]_{dist_name}", "n": n,
-                       "segments": BATCH_SEGMENTS, "lengths": "log-uniform", "seed": 0, "partition": 10},
-            "looped_plain": {"value": n / (loop_ms / 1e3), "unit": "keys/s", "ms": loop_ms,
-                             "calls": BATCH_SEGMENTS},
-            "speedup_vs_looped": loop_ms / ms_max,
-            "gpu_launches": launches, "clocks": clk.summary(), "device_ok": ok,
+            "config": {"workload": f"batch_{BATCH_SEGMENTS}x[{BATCH_LO},{args.batch_hi}]_{dist_name}",
+                       "n": rec["n"], "segments": BATCH_SEGMENTS, "lengths": "log-uniform", "seed": 0,
+                       "partition": 10},
+            "looped_plain": rec["looped_plain"], "speedup_vs_looped": rec["speedup_vs_looped"],
+            "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"], "device_ok": rec["device_ok"],
+            "segments_sorted": rec["segments_sorted"],
         }), flush=True)
+
+
+def serve_measure(dev, rate: float, duration: float, serial_too: bool = True, seed: int = 0) -> dict:
+    """Config 5: Poisson arrivals at `rate` for `duration` seconds, int32 or
+    uint64 (50/50), lengths log-uniform in [1024, 2^26], 64 GB HBM budget,
+    continuous batching; with the serial plain sort of the same stream."""
+    import torch
+
+    from paper_2003_01216_gb300 import serve
+
+    reqs = serve.make_requests(rate, duration, 1024, 1 << 26, seed=seed)
+    offered = sum(r.n for r in reqs) / duration
+    # warm up: the kernels and the caching allocator see each path once
+    warm = serve.make_requests(1000.0, 0.02, 1024, 1 << 22, seed=99)
+    serve.Server(slots=8, seed=99).run(warm)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        clk.mark()
+        st = serve.Server(slots=8, budget_bytes=64 << 30, seed=seed).run(reqs)
+        clk.done()
+    ser = serve.serial(reqs, seed=seed) if serial_too else None
+    return {"workload": f"serve_poisson{rate:g}_{duration:g}s_len[1024,2^26]_i32u64", "requests": len(reqs),
+            "offered_keys_per_s": offered, "budget_bytes": 64 << 30, "slots": 8, "small_keys": 1 << 20,
+            "served": st, "serial_plain": ser, "saturated": st["keys_per_s"] < 0.95 * offered,
+            "clocks": clk.summary()}
 
 
 def run_serve(args, rank, world, dev):
     """Serving: Poisson arrivals at --rate for --duration seconds, int32 or
     uint64 (50/50), lengths log-uniform in [1024, 2^26], 64 GB HBM budget;
     continuous batching against the serial plain sort of the same stream."""
-    import torch
-
-    from paper_2003_01216_gb300 import serve
-
-    reqs = serve.make_requests(args.rate, args.duration, 1024, 1 << 26, seed=rank)
-    offered = sum(r.n for r in reqs) / args.duration
-    # warm up: the kernels and the caching allocator see each path once
-    warm = serve.make_requests(1000.0, 0.02, 1024, 1 << 22, seed=99)
-    serve.Server(slots=8, seed=99).run(warm)
-    torch.cuda.synchronize()
-    with ClockSampler(dev.index) as clk:
-        barrier(world, dev)
-        clk.mark()
-        st = serve.Server(slots=8, budget_bytes=64 << 30, seed=rank).run(reqs)
-        clk.done()
-        barrier(world, dev)
-    ser = None if args.no_serial else serve.serial(reqs, seed=rank)
-    keys_s = reduce_max(-st["keys_per_s"], world, dev)  # min over ranks
+    barrier(world, dev)
+    rec = serve_measure(dev, args.rate, args.duration, serial_too=not args.no_serial, seed=rank)
+    barrier(world, dev)
+    keys_s = reduce_max(-rec["served"]["keys_per_s"], world, dev)  # min over ranks
     if rank == 0:
         print(json.dumps({
             "metric": "serving: keys/s and p50/p99 latency (ms) under Poisson arrivals",
             "value": world * -keys_s, "unit": "keys/s", "n_gpus": world, "steps": 1, "warmup": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+u64",
             "data": "synthetic",
-            "config": {"workload": f"serve_poisson{args.rate:g}_{args.duration:g}s_len[1024,2^26]_i32u64",
-                       "requests": len(reqs), "offered_keys_per_s": offered, "budget_bytes": 64 << 30,
-                       "slots": 8, "small_keys": 1 << 20},
-            "served": st, "serial_plain": ser,
-            "saturated": st["keys_per_s"] < 0.95 * offered,
-            "clocks": clk.summary(),
+            "config": {k: rec[k] for k in ("workload", "requests", "offered_keys_per_s", "budget_bytes", "slots",
+                                           "small_keys")},
+            "served": rec["served"], "serial_plain": rec["serial_plain"], "saturated": rec["saturated"],
+            "clocks": rec["clocks"],
         }), flush=True)
 
 

@@ -265,11 +265,14 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
     int cls = 0;
     if (img == 0) {
       if (wid == NW - 1 && b + 1 < b1) issue(b + 1, st ^ 1);
-      const bool ok = mbar_wait_bounded(&s_bar[st], st ? par1 : par0, tb.err, 2000000000ull);
+      const uint32_t ph = st ? par1 : par0;
+      const bool ok = mbar_wait_bounded(&s_bar[st], ph, tb.err, 2000000000ull);
       if (st) par1 ^= 1; else par0 ^= 1;
       if (__syncthreads_or(!ok)) {
-        // the other stage may still be loading: bounded wait, then leave
-        mbar_wait_bounded(&s_bar[st ^ 1], st ? par0 : par1, tb.err, 2000000000ull);
+        // copies may still be landing in this stage, and in the other one
+        // when the next block's copy was issued: bounded waits, then leave
+        mbar_wait_bounded(&s_bar[st], ph, tb.err, 2000000000ull);
+        if (b + 1 < b1) mbar_wait_bounded(&s_bar[st ^ 1], st ? par0 : par1, tb.err, 2000000000ull);
         return;
       }
       const K* region = reinterpret_cast<const K*>(s_raw + st * STAGE) + phase_of(keys + beg);

@@ -76,3 +76,20 @@ def test_traffic_record_scales_and_expires():
     else:  # sources changed since the capture: no traffic figure
         assert got is None
     assert bench.ncu_traffic("no_such_kernel", 1000.0) is None
+
+
+def test_per_kernel_roofline_fractions():
+    # 2^28 int32 keys: hist reads 1 GiB, scatter and tile sort move 2 GiB each,
+    # 14 merge passes over 2^28 active keys move 28 GiB; two steps were timed
+    n = 1 << 28
+    per_kernel = {"hist": (2, 0.8), "scatter": (2, 1.0), "tilesort": (2, 4.0), "merge": (28, 9.0),
+                  "corank": (28, 0.9)}
+    r = bench.per_kernel_roofline(per_kernel, 2, 4 * n, 4 * n, 14 * n, 4, "merge", 6800.0)
+    assert set(r) == {"hist", "scatter", "tilesort", "merge"}
+    assert r["hist"]["bytes_per_step"] == 4 * n
+    assert abs(r["hist"]["achieved_gbs"] - 4 * n / 0.4e-3 / 1e9) < 1e-6
+    assert abs(r["merge"]["frac"] - (2 * 4 * 14 * n / 4.5e-3 / 1e9) / 6800.0) < 1e-9
+    assert abs(r["scatter"]["frac_vs_nominal"] - (8 * n / 0.5e-3 / 1e9) / bench.NOMINAL_HBM_GBS) < 1e-9
+    assert r["merge"]["launches_per_step"] == 14
+    # a kernel that was not timed is left out
+    assert "tilesort" not in bench.per_kernel_roofline({"merge": (1, 1.0)}, 1, 1, 1, 1, 4, "merge", 1.0)

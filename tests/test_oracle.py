@@ -241,6 +241,44 @@ def test_tile_sort_intermediate(oracle):
             np.testing.assert_array_equal(ts[lo:hi], np.sort(lay[lo:hi]))
 
 
+TILE_PAIR_CASES = [
+    # (distribution, n, reduce keys modulo, tile): ties-heavy keys, tiles that
+    # do not divide the packets (a ragged last tile in every packet)
+    ("distinct16", 9_001, None, 512),
+    ("distinct16", 9_001, None, 3840),
+    ("distinct2p24", 7_777, 997, 700),
+    ("distinct2p24", 7_777, 5, 64),
+    ("uniform1e9", 6_000, 50, 1000),
+    ("int32full", 5_003, 7, 333),
+]
+
+
+@pytest.mark.parametrize("dist,n,mod,tile", TILE_PAIR_CASES)
+def test_tile_sort_pairs_is_stable_per_tile(oracle, dist, n, mod, tile):
+    # The key-value tile sort (Sec. 3.2 with the stable reading for pairs):
+    # every tile of every packet, on its own, in the order of a stable sort by
+    # key, equal keys in their packet-layout order.  numpy's stable argsort of
+    # each tile is the independent statement of that order.
+    keys = I.generate(dist, n, seed=11)
+    if mod is not None:
+        keys = keys % keys.dtype.type(mod)
+    vals = I.index_values(n)
+    lay, lv, off = oracle.partition(keys, vals, 10)
+    tk, tv = oracle.tile_sort(lay, off, tile, lv)
+    ntiles = 0
+    for p in range(off.size - 1):
+        for lo in range(int(off[p]), int(off[p + 1]), tile):
+            hi = min(lo + tile, int(off[p + 1]))
+            order = np.argsort(lay[lo:hi], kind="stable")
+            np.testing.assert_array_equal(tk[lo:hi], lay[lo:hi][order])
+            np.testing.assert_array_equal(tv[lo:hi], lv[lo:hi][order])
+            ntiles += 1
+    nonempty = int(np.count_nonzero(np.diff(off.astype(np.int64))))
+    assert ntiles > nonempty  # some packet has several tiles and a ragged last one
+    # ties are really present inside tiles (the case stability decides)
+    assert np.unique(lay).size < n // 2
+
+
 @pytest.mark.parametrize("dist", ["uniform31", "int32full", "uniform64", "distinct16"])
 def test_one_packet_is_the_plain_hybrid(oracle, dist):
     # nbuckets = 1: no MSD step, the whole array is one packet (Sec. 3.2 alone);

@@ -38,6 +38,10 @@ MUTANTS = {
     "digits_off_by_one": ("while (v >= 10) {", "while (v > 10) {"),
     # tree merge reads the neighbour's list from the wrong part
     "tree_wrong_neighbour": ("uint64_t lo = b[m], mid = b[m + w],", "uint64_t lo = b[m], mid = b[m + w / 2 + (w == 1)],"),
+    # key-value tile sort loses its tile-local index tie-break: equal keys of a
+    # tile no longer keep their packet-layout order
+    "tile_sort_no_tiebreak": ("r[i - lo] = Rec<K>{keys[i], vals[i], static_cast<uint32_t>(i - lo)};",
+                              "r[i - lo] = Rec<K>{keys[i], vals[i], 0u};"),
 }
 
 
@@ -60,6 +64,8 @@ def battery(o) -> list[str]:
     for dist in ("uniform31", "int32full", "uniform64"):
         run("invariants:" + dist, T.test_invariants_random, dist, 10)
     run("thread_count", T.test_thread_count_independence, "distinct16")
+    for case in T.TILE_PAIR_CASES:
+        run("tile_sort_pairs", T.test_tile_sort_pairs_is_stable_per_tile, *case)
     return failed
 
 
