@@ -285,12 +285,13 @@ def workload_config(args, dist, n, has_vals, world=1):
     """The workload both arms report (same keys in the GPU and the reference line)."""
     import paper_2003_01216_gb300 as hs
     code = 2 if dist in ("uniform64", "distinct2p24") else 0
-    pl = hs.plan(code, n, has_vals, fan_in=args.fan_in)
+    pl = hs.plan(code, n, has_vals, fan_in=args.fan_in, tile=getattr(args, "tile", 0))
     tile, fan = pl["tile"], pl["fan_in"]
     return {"workload": f"{args.workload}_{n}_{dist}_{args.partition}pkt", "n": n, "dist": dist,
             "key_dtype": "uint64" if dist in ("uniform64", "distinct2p24") else "int32",
             "values": "uint32 input index" if has_vals else None, "partition": args.partition,
-            "tile": tile, "fan_in": fan, "seed": 0, "parallelism": f"replicas{world}",
+            "tile": tile, "fan_in": fan, "merge": getattr(args, "merge", "queue"), "seed": 0,
+            "parallelism": f"replicas{world}",
             "l2": "inputs larger than L2 (>= 1 GiB vs 129 MB); a 1 GiB restore copy between timed steps"}
 
 
@@ -307,6 +308,9 @@ def main():
     ap.add_argument("--partition", type=int, default=10)
     ap.add_argument("--fan-in", type=int, default=0, help="runs per merge pass: 2 or 4 (0 = library default)")
     ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--merge", default="queue", choices=["queue", "per_pass"],
+                    help="two-way merge passes as one persistent queue launch, or two launches per pass (ablation)")
+    ap.add_argument("--tile", type=int, default=0, help="keys per tile (0 = library default)")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--ref-sample", type=int, default=1 << 23)
     ap.add_argument("--cpu-sample", type=int, default=1 << 25)
@@ -359,6 +363,8 @@ def main():
     pkt = torch.zeros(args.partition + 1, dtype=torch.uint64, device=dev)
     stream = torch.cuda.current_stream()
 
+    dbg = 4 if args.merge == "per_pass" else 0
+
     def restore():
         work.copy_(pristine)
         if has_vals:
@@ -368,9 +374,11 @@ def main():
         # the packet offsets are an optional extra output (the byte model reads
         # them); the timed steps sort the way a caller without it would
         if has_vals:
-            hs.sort_pairs(work, vals, partition=args.partition, packet_offsets=offsets, fan_in=args.fan_in)
+            hs.sort_pairs(work, vals, partition=args.partition, packet_offsets=offsets, fan_in=args.fan_in,
+                          tile=args.tile, debug_flags=dbg)
         else:
-            hs.sort_keys(work, partition=args.partition, packet_offsets=offsets, fan_in=args.fan_in)
+            hs.sort_keys(work, partition=args.partition, packet_offsets=offsets, fan_in=args.fan_in, tile=args.tile,
+                         debug_flags=dbg)
 
     # warm-up (also sizes the work space outside the timed region; the last
     # one returns the packet offsets, identical for every step of one input)
@@ -379,7 +387,7 @@ def main():
         step(pkt if w == args.warmup - 1 else None)
     if hs.stream_error() != 0:
         raise RuntimeError("device error during warm-up")
-    plan = hs.plan(hs.dtype_code(work), n, has_vals, 1, args.partition, fan_in=args.fan_in)
+    plan = hs.plan(hs.dtype_code(work), n, has_vals, 1, args.partition, fan_in=args.fan_in, tile=args.tile)
     mk = "merge4" if plan["fan_in"] == 4 else "merge"
 
     # timed region: K steps, each bracketed by events on the launching stream
@@ -432,10 +440,13 @@ def main():
     peak, peak_kind = load_peaks()
     pkt_np = pkt.cpu().numpy()
     active = merge_active_keys(pkt_np, plan["tile"], plan["fan_in"])
+    if "merge_sched" in per_kernel:  # every merge pass in one persistent launch
+        mk = "merge_sched"
     merge_launches, merge_ms = per_kernel.get(mk, (0, 0.0))
     merge_bytes = 2 * s * sum(active) * split_steps  # each pass reads and writes its active keys
     achieved = merge_bytes / (merge_ms / 1e3) / 1e9 if merge_ms > 0 else None
-    keys_per_launch = sum(active) / max(1, len(active))
+    # keys of the merge passes one launch covers (all of them for the scheduler)
+    keys_per_launch = sum(active) if mk == "merge_sched" else sum(active) / max(1, len(active))
     traffic = ncu_traffic(mk, keys_per_launch)
     b_alg = s * n * 1 + 2 * s * n + 2 * s * n + 2 * s * sum(active)  # hist + scatter + tile sort + merges
     whole_gbs = b_alg / (mean_ms / 1e3) / 1e9
@@ -515,7 +526,8 @@ def main():
         dist.destroy_process_group()
 
 
-def batch_measure(dev, hi: int, steps: int, warmup: int, dist_name: str = "uniform31", world: int = 1) -> dict:
+def batch_measure(dev, hi: int, steps: int, warmup: int, dist_name: str = "uniform31", world: int = 1,
+                  debug_flags: int = 0) -> dict:
     """Config 4: 10,000 int32 segments, lengths log-uniform in [16, hi], sorted
     by one hs_sort_batch call (one CUDA-graph launch), against the plain sort
     looped over the segments on the same stream and data.  Returns the timing
@@ -535,7 +547,7 @@ def batch_measure(dev, hi: int, steps: int, warmup: int, dist_name: str = "unifo
     with torch.cuda.stream(st):
         for _ in range(warmup):
             work.copy_(pristine)
-            hs.sort_batch(work, offs, graph=True)
+            hs.sort_batch(work, offs, graph=True, debug_flags=debug_flags)
         if hs.stream_error(st) != 0:
             raise RuntimeError("device error during warm-up")
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -547,7 +559,7 @@ def batch_measure(dev, hi: int, steps: int, warmup: int, dist_name: str = "unifo
             for i in range(steps):
                 work.copy_(pristine)
                 ev[i][0].record(st)
-                hs.sort_batch(work, offs, graph=True)
+                hs.sort_batch(work, offs, graph=True, debug_flags=debug_flags)
                 ev[i][1].record(st)
             torch.cuda.synchronize()
             clk.done()
@@ -555,13 +567,13 @@ def batch_measure(dev, hi: int, steps: int, warmup: int, dist_name: str = "unifo
         ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
         ok = hs.stream_error(st) == 0
         # every segment sorted (device-side property check of the last step)
-        lo_t, hi_t = offs[:-1], offs[1:]
         d = work[1:] >= work[:-1]
         inner = torch.ones_like(d)
-        starts = lo_t[(lo_t > 0) & (lo_t < n)].long() - 1  # pairs that straddle a segment start
-        inner[starts] = False
+        lo_np = off_h[:-1].astype(np.int64)
+        starts = lo_np[(lo_np > 0) & (lo_np < n)] - 1  # pairs that straddle a segment start
+        inner[torch.from_numpy(starts).to(dev)] = False
         sorted_ok = bool((d | ~inner).all().item())
-        del hi_t
+        del d, inner
         # the same segments through the plain per-array call, looped on one stream
         work.copy_(pristine)
         lo_ = [int(x) for x in off_h]
@@ -585,7 +597,8 @@ def batch_measure(dev, hi: int, steps: int, warmup: int, dist_name: str = "unifo
 def run_batch(args, rank, world, dev, dist_name):
     """Batched sort (one CUDA-graph launch for all segments) against the plain
     sort looped over the segments, same stream, same data."""
-    rec = batch_measure(dev, args.batch_hi, args.steps, args.warmup, dist_name, world)
+    rec = batch_measure(dev, args.batch_hi, args.steps, args.warmup, dist_name, world,
+                        4 if args.merge == "per_pass" else 0)
     if rank == 0:
         print(json.dumps({
             "metric": "batched sort throughput (keys/s): one graph launch over all segments",

@@ -66,9 +66,12 @@ typedef struct {
   int partition;        /* 10 (default): MSD decimal packets (Sec. 3.4); 256: top-8-bit ablation;
                            1: no MSD step, the whole array is one packet (the shared-memory
                            hybrid of Sec. 3.2 alone; ablation) */
-  int tile;             /* keys per tile of the per-packet sort; 0 = the built tile for the call
-                           (7936 for 4-byte keys without values, else 3840; see hs_plan_describe).
-                           Any other value returns HS_ERR_UNSUPPORTED */
+  int tile;             /* keys per tile of the per-packet sort (= 256 threads x items per thread;
+                           also the outputs of one merge block).  Built tiles (hs_tiles): 3840,
+                           5888 and 7936 for 4-byte keys without values; 2816 and 3840 otherwise.
+                           0 = tuned: the tuning table's entry (hs_tune_set_shape), else 7936
+                           for 4-byte keys without values and 3840 otherwise.  A tile not built
+                           for the call's key type returns HS_ERR_UNSUPPORTED */
   int fan_in;           /* runs merged per merge pass (Fig. 1(b) merges two): 2, or 4 (every
                            pass merges groups of four adjacent runs, so half the passes over
                            memory; same result bit for bit), or 0 = tuned: the entry of the
@@ -220,6 +223,20 @@ hs_status hs_graph_cache_clear(void);
 hs_status hs_tune_set(hs_dtype dtype, int has_vals, int partition, int log2n, int fan_in);
 hs_status hs_tune_get(hs_dtype dtype, int has_vals, int partition, size_t n, int* fan_in);
 hs_status hs_tune_clear(void);
+
+/* Tuning table, whole shape: the merge fan-in (2, 4, or 0 = the built-in rule)
+ * and the tile (a built tile of the key type, or 0 = the default tile) that
+ * calls with opts->fan_in == 0 / opts->tile == 0 use for this (key type, has
+ * values, partition, size bucket = ceil(log2(n))).  The shape changes only how
+ * the work is cut (tile sort, merge blocks, passes), never the result, which is
+ * the sorted order of Sec. 3.4 bit for bit.  Invalid values: HS_ERR_INVALID.
+ * hs_tune_get_shape: the shape a call for n keys would use. */
+hs_status hs_tune_set_shape(hs_dtype dtype, int has_vals, int partition, int log2n, int fan_in, int tile);
+hs_status hs_tune_get_shape(hs_dtype dtype, int has_vals, int partition, size_t n, int* fan_in, int* tile);
+
+/* The tiles built for a key type (and values): writes up to `max` of them to
+ * `tiles` (ascending) and their number to *count. */
+hs_status hs_tiles(hs_dtype dtype, int has_vals, int* tiles, int max, int* count);
 
 /* Cumulative number of kernel launches this library has enqueued in this
  * process (memsets and copies not counted; a graph replay counts the kernels

@@ -45,7 +45,7 @@ def _check_dev(*ts):
             raise ValueError("tensor must be contiguous")
 
 
-def _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph=False, fan_in=0):
+def _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph=False, fan_in=0, tile=0):
     po = 0
     if packet_offsets is not None:
         _check_dev(packet_offsets)
@@ -55,39 +55,41 @@ def _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph=F
         _check_dev(workspace)
         wp, wb = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     return N.make_opts(partition=partition, stop_after=stop_after, packet_offsets_ptr=po, workspace_ptr=wp,
-                       workspace_bytes=wb, debug_flags=debug_flags, graph=graph, fan_in=fan_in)
+                       workspace_bytes=wb, debug_flags=debug_flags, graph=graph, fan_in=fan_in, tile=tile)
 
 
 def sort_keys(keys, partition: int = 10, stop_after: int = 0, packet_offsets=None, stream=None,
-              debug_flags: int = 0, workspace=None, graph: bool = False, fan_in: int = 0):
+              debug_flags: int = 0, workspace=None, graph: bool = False, fan_in: int = 0, tile: int = 0):
     """Sort a CUDA tensor of int32/uint32/uint64 keys in place (ascending).
-    fan_in: runs merged per merge pass, 2 or 4 (0 = the library default)."""
+    fan_in: runs merged per merge pass, 2 or 4; tile: keys per tile, one of
+    tiles(dtype) (0 = the tuned or default shape)."""
     _check_dev(keys)
-    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in)
+    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in, tile)
     N.check(N.lib().hs_sort_keys(dtype_code(keys), keys.data_ptr(), keys.numel(), ctypes.byref(o), _stream(stream)),
             "hs_sort_keys")
     return keys
 
 
 def sort_pairs(keys, vals, partition: int = 10, stop_after: int = 0, packet_offsets=None, stream=None,
-               debug_flags: int = 0, workspace=None, graph: bool = False, fan_in: int = 0):
+               debug_flags: int = 0, workspace=None, graph: bool = False, fan_in: int = 0, tile: int = 0):
     """Stable in-place sort of (key, uint32 value) pairs by key."""
     import torch
     _check_dev(keys, vals)
     if vals.dtype not in (torch.uint32, torch.int32) or vals.numel() != keys.numel():
         raise ValueError("vals must be a uint32 (or int32) tensor as long as keys")
-    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in)
+    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in, tile)
     N.check(N.lib().hs_sort_pairs(dtype_code(keys), keys.data_ptr(), vals.data_ptr(), keys.numel(), 1,
                                   ctypes.byref(o), _stream(stream)), "hs_sort_pairs")
     return keys, vals
 
 
 def sort_batch(keys, offsets, vals=None, partition: int = 10, stop_after: int = 0, packet_offsets=None,
-               stream=None, workspace=None, graph: bool = False, fan_in: int = 0):
+               stream=None, workspace=None, graph: bool = False, fan_in: int = 0, tile: int = 0,
+               debug_flags: int = 0):
     """Sort every segment [offsets[s], offsets[s+1]) of `keys` on its own.
     offsets: CUDA uint64 (or int64) tensor of nseg + 1 entries."""
     _check_dev(keys, offsets, vals)
-    o = _opts(partition, stop_after, packet_offsets, 0, workspace, graph, fan_in)
+    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in, tile)
     nseg = offsets.numel() - 1
     vp = vals.data_ptr() if vals is not None else None
     N.check(N.lib().hs_sort_batch(dtype_code(keys), keys.data_ptr(), vp, offsets.data_ptr(), nseg, keys.numel(),
@@ -116,10 +118,18 @@ def stream_error(stream=None) -> int:
     return N.lib().hs_stream_error(_stream(stream))
 
 
+def tiles(dtype: int, has_vals: bool = False) -> list[int]:
+    """The tile sizes (keys) built for a key type, ascending."""
+    out = (ctypes.c_int * 8)()
+    c = ctypes.c_int()
+    N.check(N.lib().hs_tiles(dtype, int(has_vals), out, 8, ctypes.byref(c)), "hs_tiles")
+    return [out[i] for i in range(c.value)]
+
+
 def plan(dtype: int, n: int, has_vals: bool = False, nseg: int = 1, partition: int = 10, stop_after: int = 0,
-         fan_in: int = 0):
+         fan_in: int = 0, debug_flags: int = 0, tile: int = 0):
     p = N.HsPlan()
-    o = N.make_opts(partition=partition, stop_after=stop_after, fan_in=fan_in)
+    o = N.make_opts(partition=partition, stop_after=stop_after, fan_in=fan_in, debug_flags=debug_flags, tile=tile)
     N.check(N.lib().hs_plan_describe(dtype, n, int(has_vals), nseg, ctypes.byref(o), ctypes.byref(p)),
             "hs_plan_describe")
     return {"tile": p.tile, "part_tile": p.part_tile, "merge_passes": p.merge_passes, "launches": p.launches,

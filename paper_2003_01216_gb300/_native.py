@@ -21,6 +21,7 @@ EXPORTS = [
     "hs_workspace_reserve", "hs_workspace_release", "hs_stream_error", "hs_plan_describe",
     "hs_timing_enable", "hs_timing_read", "hs_kernel_launches", "hs_status_string", "hs_last_error",
     "hs_sort_keys_noalloc", "hs_graph_cache_clear", "hs_tune_set", "hs_tune_get", "hs_tune_clear",
+    "hs_tune_set_shape", "hs_tune_get_shape", "hs_tiles",
 ]
 
 
@@ -83,6 +84,9 @@ def lib() -> ctypes.CDLL:
         L.hs_tune_set.argtypes = [i, i, i, i, i]
         L.hs_tune_get.argtypes = [i, i, i, sz, p]
         L.hs_tune_clear.argtypes = []
+        L.hs_tune_set_shape.argtypes = [i, i, i, i, i, i]
+        L.hs_tune_get_shape.argtypes = [i, i, i, sz, p, p]
+        L.hs_tiles.argtypes = [i, i, p, i, p]
         L.hs_stream_error.argtypes = [p]
         L.hs_plan_describe.argtypes = [i, sz, i, sz, p, p]
         L.hs_timing_enable.argtypes = [i]

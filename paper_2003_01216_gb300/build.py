@@ -21,12 +21,26 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
 
+# (key type, tag, items per thread) of every tile shape built: sort_shape.cu
+# is compiled once per shape (see driver.cuh for the shapes)
+SHAPES = [("int32_t", "i32", t) for t in (11, 15, 23, 31)] + [("uint32_t", "u32", t) for t in (11, 15, 23, 31)] + \
+    [("uint64_t", "u64", t) for t in (11, 15)]
+
+
+def _shape_objs() -> list[tuple[str, str, list[str]]]:
+    """(object name, source, defines) of the per-shape translation units."""
+    return [(f"sort_{tag}_t{ipt}.o", "sort_shape.cu",
+             [f"-DHS_SHAPE_KEY={key}", f"-DHS_SHAPE_IPT={ipt}", f"-DHS_SHAPE_FN=run_sort_{tag}_t{ipt}"])
+            for key, tag, ipt in SHAPES]
+
+
+# library -> [(object, source, defines)]
 LIBS = {
-    "libhsort.so": ["hsort_abi.cu", "hsort_noalloc.cu", "sort_i32.cu", "sort_u32.cu", "sort_u64.cu"],
-    "libhsgen.so": ["gen.cu"],
+    "libhsort.so": [("hsort_abi.o", "hsort_abi.cu", []), ("hsort_noalloc.o", "hsort_noalloc.cu", [])] + _shape_objs(),
+    "libhsgen.so": [("gen.o", "gen.cu", [])],
 }
 HEADERS = ["common.cuh", "async.cuh", "scan.cuh", "partition.cuh", "blockmerge.cuh", "tilesort.cuh", "merge.cuh", "merge4.cuh",
-           "driver.cuh", "runtime.h"]
+           "sched.cuh", "driver.cuh", "runtime.h"]
 
 
 def nvcc() -> str:
@@ -38,12 +52,12 @@ def _newer(out: str, deps: list[str]) -> bool:
     return os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(d) for d in deps)
 
 
-def _compile(src: str, verbose: bool, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+def _compile(obj_name: str, src: str, defines: list[str], verbose: bool, extra: list[str]) -> str:
+    obj = os.path.join(BUILD, obj_name)
     deps = [src] + [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "hsort.h")]
     if _newer(obj, deps) and not extra:
         return obj
-    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *FLAGS, *defines, *extra, "-c", src, "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.run(cmd, check=True)
@@ -54,13 +68,14 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> dict[str, st
     """Compile every library; returns {name: path}."""
     extra = list(extra or [])
     os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted({s for v in LIBS.values() for s in v})
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        objs = dict(zip(srcs, ex.map(lambda s: _compile(os.path.join(CSRC, s), verbose, extra), srcs)))
+    units = {o: (s, d) for parts in LIBS.values() for o, s, d in parts}
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        objs = dict(zip(units, ex.map(
+            lambda o: _compile(o, os.path.join(CSRC, units[o][0]), units[o][1], verbose, extra), units)))
     out = {}
     for lib, parts in LIBS.items():
         path = os.path.join(PKG, lib)
-        ol = [objs[p] for p in parts]
+        ol = [objs[o] for o, _, _ in parts]
         if not _newer(path, ol) or extra:
             cmd = [nvcc(), *ARCH, "-shared", "-o", path, *ol]
             if verbose:

@@ -200,6 +200,9 @@ struct Tables {
   uint32_t* seg_flip;     // nseg: sign flip in use
   uint64_t* pkt_off;      // nseg * NB + 1 absolute packet starts
   uint32_t* unit_prefix;  // nseg * NB + 1: first tile of each packet (tile = merge block)
+  uint32_t* small_before; // nseg + 1: keys of short segments (sorted whole by one CTA) before each segment
+  uint32_t* small_list;   // nseg: the short segments, in order
+  uint32_t* small_cnt;    // 1 word: number of short segments
   uint32_t* err;          // device error word
   int fan_log2;           // log2 of the merge fan-in: 1 (two runs per merge) or 2 (four)
 };

@@ -1,6 +1,6 @@
 // Host side of one sort call: work-space layout and the launch sequence.
-// Included by one translation unit per key type (sort_i32.cu, sort_u32.cu,
-// sort_u64.cu) so the three compile in parallel.
+// Included by one translation unit per (key type, tile shape): sort_shape.cu
+// compiled once per pair, so they compile in parallel.
 #pragma once
 #include <algorithm>
 #include <cstdio>
@@ -13,6 +13,7 @@
 #include "merge.cuh"
 #include "merge4.cuh"
 #include "tilesort.cuh"
+#include "sched.cuh"
 #include "runtime.h"
 
 namespace hs {
@@ -22,20 +23,34 @@ constexpr int kBlock = 256;     // threads per CTA of every heavy kernel
 constexpr int kIpt = 15;        // items per thread of the packet step (odd: conflict-free blocked access)
 constexpr int kTile = kBlock * kIpt;  // keys per packet-step block
 
-// Items per thread of the tile sort and the merge passes: 31 for 4-byte keys
-// without values (twice the work per co-rank search and per block, one merge
-// pass fewer), 15 where 31 items and their companions would not fit in
-// registers.  Odd, so blocked shared-memory access is conflict-free.
+// Tile shapes (items per thread of the tile sort and the merge passes; a
+// tile is kBlock x IPT keys), all odd so blocked shared-memory access is free
+// of bank conflicts.  Built: 15, 23 and 31 for 4-byte keys without values;
+// 11 and 15 otherwise (where 31 items and their companions would not fit in
+// registers).  Default (no tuning-table entry, hs_opts.tile = 0): 31 for
+// 4-byte keys without values (twice the work per co-rank search and per
+// block of 15, one merge pass fewer), 15 otherwise.
 template <class K, bool HAS_V>
 constexpr int sort_ipt() {
   return (sizeof(K) == 4 && !HAS_V) ? 31 : 15;
 }
-template <class K, bool HAS_V>
-constexpr int sort_tile() {
-  return kBlock * sort_ipt<K, HAS_V>();
+template <class K, bool HAS_V, int IPT>
+constexpr bool ipt_built() {
+  return (sizeof(K) == 4 && !HAS_V) ? (IPT == 15 || IPT == 23 || IPT == 31) : (IPT == 11 || IPT == 15);
+}
+constexpr int kTileIpts[] = {11, 15, 23, 31};
+inline bool tile_built(size_t key_bytes, bool has_vals, int tile) {
+  const bool wide = key_bytes == 4 && !has_vals;
+  return wide ? (tile == kBlock * 15 || tile == kBlock * 23 || tile == kBlock * 31)
+              : (tile == kBlock * 11 || tile == kBlock * 15);
 }
 inline int sort_tile_for(size_t key_bytes, bool has_vals) {
   return kBlock * ((key_bytes == 4 && !has_vals) ? 31 : 15);
+}
+// the smallest built tile: work-space tables are sized for it, so one work
+// space serves every tile shape of its key type
+inline int min_tile_for(size_t key_bytes, bool has_vals) {
+  return kBlock * ((key_bytes == 4 && !has_vals) ? 15 : 11);
 }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -47,14 +62,24 @@ constexpr int kMaxPasses = 64;
 inline int corank_group(size_t units) { return units <= 4096 ? 16 : (units <= 16384 ? 4 : 1); }
 constexpr int kMerge4Spt = 2;  // fan-in-4 merge: chunk slots per tile (average chunk = tile / slots)  // pass-control words (n < 2^32 needs at most 32 passes)
 
+// Worst-case merge passes for a packet of up to n keys, sorted in tiles of
+// `tile`, merged `fan_in` runs at a time.
+inline int worst_passes(size_t n, size_t tile, int fan_in = 2) {
+  size_t tiles = (n + tile - 1) / tile;
+  int p = 0;
+  while ((static_cast<size_t>(1) << p) < tiles) ++p;
+  return fan_in == 4 ? (p + 1) / 2 : p;
+}
+
 struct Layout {
   size_t keys_w, vals_w, seg_off, blk_prefix, cls_raw, cnt_raw, flat, scan_part, seg_neg, seg_cmax, seg_class,
-      seg_flip, pkt_off, unit_prefix, recs, list, any_neg, pass_ctl, zero, zero_bytes, total;
+      seg_flip, pkt_off, unit_prefix, recs, list, any_neg, pass_ctl, zero, zero_bytes, small_before, small_list,
+      small_cnt, sched, sched_bytes, total;
   uint32_t max_blocks, max_units, npk;
 };
 
 inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg, int nb) {
-  const size_t stile = sort_tile_for(key_bytes, has_vals);
+  const size_t stile = min_tile_for(key_bytes, has_vals);
   Layout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -87,6 +112,13 @@ inline Layout make_layout(size_t key_bytes, size_t n, bool has_vals, size_t nseg
   const size_t slots = static_cast<size_t>(L.max_units) * kMerge4Spt + 1;  // fan-in-4 chunk slots
   L.recs = take(std::max((static_cast<size_t>(L.max_units) + 1) * sizeof(MergeRec), slots * sizeof(Rec4)));
   L.list = take(slots * 4);
+  L.small_before = take((nseg + 1) * 4);
+  L.small_list = take(nseg * 4);
+  L.small_cnt = take(4);
+  // merge scheduler: the ticket counter (256 bytes) and one completion
+  // counter per (pass, unit) for passes 0 .. worst case
+  L.sched_bytes = 256 + static_cast<size_t>(worst_passes(n, stile) + 1) * L.max_units * 4;
+  L.sched = take(L.sched_bytes);
   L.total = off;
   return L;
 }
@@ -108,18 +140,13 @@ inline Tables make_tables(char* base, const Layout& L, uint32_t* err, int fan_lo
   t.unit_prefix = reinterpret_cast<uint32_t*>(base + L.unit_prefix);
   t.any_neg = reinterpret_cast<uint32_t*>(base + L.any_neg);
   t.pass_ctl = reinterpret_cast<uint32_t*>(base + L.pass_ctl);
+  t.small_before = reinterpret_cast<uint32_t*>(base + L.small_before);
+  t.small_list = reinterpret_cast<uint32_t*>(base + L.small_list);
+  t.small_cnt = reinterpret_cast<uint32_t*>(base + L.small_cnt);
   t.err = err;
   return t;
 }
 
-// Worst-case merge passes for a packet of up to n keys, sorted in tiles of
-// `tile`, merged `fan_in` runs at a time.
-inline int worst_passes(size_t n, size_t tile, int fan_in = 2) {
-  size_t tiles = (n + tile - 1) / tile;
-  int p = 0;
-  while ((static_cast<size_t>(1) << p) < tiles) ++p;
-  return fan_in == 4 ? (p + 1) / 2 : p;
-}
 inline int fan_log2_of(int fan_in) { return fan_in == 4 ? 2 : 1; }
 
 template <class K, bool HAS_V, int NB>
@@ -139,24 +166,24 @@ template <class K>
 inline size_t hist_smem() {  // two stages of keys
   return 2 * ((region_elems(kTile) * sizeof(K) + 127) & ~size_t(127));
 }
-template <class K, bool HAS_V>
+template <class K, bool HAS_V, int IPT>
 inline size_t sort_smem() {  // one region of keys (and values)
-  return merge_stage_bytes<K, HAS_V>(sort_tile<K, HAS_V>());
+  return merge_stage_bytes<K, HAS_V>(kBlock * IPT);
 }
 // Fan-in-4 merge shape: threads per CTA and CTAs per SM.
 constexpr int kMerge4Block = 256;
 constexpr int kMerge4MinBlocks = 3;
-template <class K, bool HAS_V>
+template <class K, bool HAS_V, int IPT>
 constexpr int merge4_cmax() {
-  return chunk_max<sort_tile<K, HAS_V>(), kMerge4Spt>();
+  return chunk_max<kBlock * IPT, kMerge4Spt>();
 }
-template <class K, bool HAS_V>
+template <class K, bool HAS_V, int IPT>
 inline size_t merge4_smem_for() {  // two stages of the largest chunk and T
-  return merge4_smem<K, HAS_V, merge4_cmax<K, HAS_V>()>();
+  return merge4_smem<K, HAS_V, merge4_cmax<K, HAS_V, IPT>()>();
 }
-template <class K, bool HAS_V>
+template <class K, bool HAS_V, int IPT>
 inline size_t merge_smem() {  // two input stages (+ two output buffers when they fit)
-  constexpr int T = sort_tile<K, HAS_V>();
+  constexpr int T = kBlock * IPT;
   return merge_buffers<K, HAS_V, T>() * merge_stage_bytes<K, HAS_V>(T);
 }
 
@@ -186,7 +213,9 @@ inline int persistent_grid(Kern kern, int block, size_t smem) {
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  // (opt in whenever dynamic shared memory is used: static plus dynamic above
+  // 48 KB needs it even when the dynamic part alone is below)
+  if (smem > 0) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem);
   if (occ < 1) occ = 1;
   return sms * occ;
@@ -220,7 +249,7 @@ hs_status launch_bound4(Launcher& lc, K* keys, K* kw, Rec4* recs, uint32_t* list
 // One sort call.  keys/vals: the caller's arrays (U).  offs: batch offsets
 // (device) or nullptr for one segment.  ws: work space of at least
 // make_layout(...).total bytes.
-template <class K, bool HAS_V, int NB>
+template <class K, bool HAS_V, int NB, int IPT>
 hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
                       char* ws, uint32_t* err, cudaStream_t st) {
   const Layout L = make_layout(sizeof(K), n, HAS_V, nseg, NB);
@@ -233,22 +262,32 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
 
   // zero the per-segment flags and maxima and the pass control (one region)
   HS_TRY(lc.memset("zero_tables", ws + L.zero, 0, L.zero_bytes));
+  // the merge scheduler's ticket and completion counters
+  const bool use_sched = fan == 2 && !(o.debug_flags & 4) && o.stop_after != 1 && o.stop_after != 2 &&
+                         worst_passes(n, (kBlock * IPT)) > 0;
+  if (use_sched) HS_TRY(lc.memset("zero_sched", ws + L.sched, 0, L.sched_bytes));
   const bool small = static_cast<uint64_t>(L.max_blocks) * NB <= kPlanSmallEntries &&
                      static_cast<uint64_t>(L.npk) <= kPlanSmallEntries;
 
-  HS_TRY(lc.kernel("seg_plan", k_seg_plan, 1, 1024, 0, offs, nseg32, n, kTile, tb));
+  // Short segments (at most one tile) are sorted whole by one CTA of the tile
+  // sort launch; not when a testing stop point asks for the packet layout or
+  // the tile sort's state.
+  const uint32_t small_max = o.stop_after == 0 ? static_cast<uint32_t>((kBlock * IPT)) : 0u;
+  // one segment known on the host to be short: no packet-step kernels at all
+  const bool all_short = nseg == 1 && n <= small_max;
+  HS_TRY(lc.kernel("seg_plan", k_seg_plan, 1, 1024, 0, offs, nseg32, n, kTile, small_max, tb));
 
   if constexpr (NB == 1) {
     // no MSD step (ablation): every segment is one packet; the tile sort
     // reads the caller's array directly
     if (small) {
-      HS_TRY(lc.kernel("plan_small", (k_plan_small<1>), 1, kPlanThreads, 0, nseg32, sort_tile<K, HAS_V>(), tb));
+      HS_TRY(lc.kernel("plan_small", (k_plan_small<1>), 1, kPlanThreads, 0, nseg32, (kBlock * IPT), tb));
     } else {
-      HS_TRY(lc.kernel("pkt", k_pkt_whole, (nseg32 + 255) / 256, 256, 0, nseg32, sort_tile<K, HAS_V>(), tb));
+      HS_TRY(lc.kernel("pkt", k_pkt_whole, (nseg32 + 255) / 256, 256, 0, nseg32, (kBlock * IPT), tb));
       HS_TRY(lc.kernel("scan_units", k_scan_units, 1, 1024, 0, L.npk, tb));
     }
   } else {
-    {
+    if (!all_short) {
       static PerDevice grid_cache;
       int& grid = grid_cache();
       const size_t smem = hist_smem<K>();
@@ -260,7 +299,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       }
     }
     if (small) {
-      HS_TRY(lc.kernel("plan_small", (k_plan_small<NB>), 1, kPlanThreads, 0, nseg32, sort_tile<K, HAS_V>(), tb));
+      HS_TRY(lc.kernel("plan_small", (k_plan_small<NB>), 1, kPlanThreads, 0, nseg32, (kBlock * IPT), tb));
     } else {
     HS_TRY(lc.kernel("finalize", (k_finalize<NB>), (nseg32 + 255) / 256, 256, 0, nseg32, tb));
     {
@@ -279,12 +318,14 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       static PerDevice grid_cache;
       int& grid = grid_cache();
       if (!grid) grid = persistent_grid(k_pkt<NB>, 256, 0);
-      HS_TRY(lc.kernel("pkt", (k_pkt<NB>), grid, 256, 0, nseg32, sort_tile<K, HAS_V>(), tb));
+      HS_TRY(lc.kernel("pkt", (k_pkt<NB>), grid, 256, 0, nseg32, (kBlock * IPT), tb));
     }
     HS_TRY(lc.kernel("scan_units", k_scan_units, 1, 1024, 0, L.npk, tb));
     }
 
-    if constexpr (NB <= 16) {
+    if (all_short) {
+      // nothing to scatter: the one segment is sorted whole by the tile sort launch
+    } else if constexpr (NB <= 16) {
       // persistent: bulk copies in and out, ranks from one scan of packed counts
       static PerDevice grid_cache;
       int& grid = grid_cache();
@@ -317,25 +358,27 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     {
       static PerDevice grid_cache;
       int& grid = grid_cache();
-      const size_t smem = sort_smem<K, HAS_V>();
-      auto kern = k_tilesort<K, HAS_V, kBlock, sort_ipt<K, HAS_V>()>;
+      const size_t smem = sort_smem<K, HAS_V, IPT>();
+      auto kern = k_tilesort<K, HAS_V, NB, kBlock, IPT>;
       if (!grid) grid = persistent_grid(kern, kBlock, smem);
       const bool stuck = (o.debug_flags & 1) != 0;
       const uint64_t limit_ns = stuck ? 2000000ull : 2000000000ull;  // 2 ms when injected, else 2 s
       const K* ts_k = (NB == 1) ? keys : kw;
       const uint32_t* ts_v = (NB == 1) ? vals : vw;
-      HS_TRY(lc.kernel("tilesort", kern, capped(grid, L.max_units), kBlock, smem, ts_k, ts_v, keys, vals, kw, vw, L.npk,
+      // work items: the tiles of the packets, then the short segments
+      const uint64_t items = static_cast<uint64_t>(L.max_units) + (small_max ? nseg : 0);
+      HS_TRY(lc.kernel("tilesort", kern, capped(grid, items), kBlock, smem, ts_k, ts_v, keys, vals, kw, vw, L.npk,
                        o.stop_after == 2 ? 1 : 0, stuck ? 1 : 0, limit_ns, tb));
     }
     if (o.stop_after == 2) {
       HS_TRY(lc.copy("copy_back", keys, kw, n * sizeof(K)));
       if (HAS_V) HS_TRY(lc.copy("copy_back_v", vals, vw, n * 4));
     } else if (fan == 4) {
-      constexpr int T = sort_tile<K, HAS_V>();
+      constexpr int T = (kBlock * IPT);
       static PerDevice mgrid_cache;
       int& mgrid = mgrid_cache();
-      const size_t smem = merge4_smem_for<K, HAS_V>();
-      auto mk = k_merge4<K, HAS_V, kMerge4Block, kMerge4MinBlocks, merge4_cmax<K, HAS_V>()>;
+      const size_t smem = merge4_smem_for<K, HAS_V, IPT>();
+      auto mk = k_merge4<K, HAS_V, kMerge4Block, kMerge4MinBlocks, merge4_cmax<K, HAS_V, IPT>()>;
       if (!mgrid) mgrid = persistent_grid(mk, kMerge4Block, smem);
       Rec4* recs = reinterpret_cast<Rec4*>(ws + L.recs);
       uint32_t* list = reinterpret_cast<uint32_t*>(ws + L.list);
@@ -347,12 +390,31 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
         HS_TRY(lc.kernel("merge4", mk, capped(mgrid, static_cast<uint64_t>(L.max_units) * kMerge4Spt), kMerge4Block,
                          smem, keys, vals, kw, vw, recs, list, r, tb));
       }
+    } else if (!(o.debug_flags & 4)) {
+      // every merge pass in one persistent launch (dependency-driven queue)
+      static PerDevice sgrid_cache;
+      int& sgrid = sgrid_cache();
+      const size_t smem = 2 * merge_stage_bytes<K, HAS_V>(kBlock * IPT);  // two stages
+      auto sk = k_merge_sched<K, HAS_V, kBlock, IPT>;
+      if (!sgrid) sgrid = persistent_grid(sk, kBlock + 32, smem);
+      const bool drop = (o.debug_flags & 2) != 0;
+      SchedArgs sa;
+      sa.ticket = reinterpret_cast<uint32_t*>(ws + L.sched);
+      sa.done = reinterpret_cast<uint32_t*>(ws + L.sched + 256);
+      sa.pass_limit = o.stop_after >= 3 ? o.stop_after - 2 : kMaxPasses;
+      sa.debug_drop = drop ? 1 : 0;
+      sa.limit_ns = drop ? 2000000ull : 2000000000ull;  // 2 ms when a completion is dropped, else 2 s
+      if (worst_passes(n, (kBlock * IPT)) > 0) {
+        HS_TRY(lc.kernel("merge_sched", sk, capped(sgrid, L.max_units), kBlock + 32, smem, keys, vals, kw, vw, L.npk,
+                         tb, sa));
+      }
     } else {
+      // per-pass launches (co-rank kernel, then merge kernel), kept as an ablation
       static PerDevice mgrid_cache;
       int& mgrid = mgrid_cache();
-      const size_t smem = merge_smem<K, HAS_V>();
-      auto mk = k_merge<K, HAS_V, kBlock, sort_ipt<K, HAS_V>()>;
-      constexpr int T = sort_tile<K, HAS_V>();
+      const size_t smem = merge_smem<K, HAS_V, IPT>();
+      auto mk = k_merge<K, HAS_V, kBlock, IPT>;
+      constexpr int T = (kBlock * IPT);
       if (!mgrid) mgrid = persistent_grid(mk, kBlock, smem);
       MergeRec* recs = reinterpret_cast<MergeRec*>(ws + L.recs);
       const int P = o.stop_after >= 3 ? std::min(worst_passes(n, T), o.stop_after - 2) : worst_passes(n, T);
@@ -365,7 +427,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       }
     }
     if (o.stop_after >= 3) {  // testing: the state after merge pass r, gathered into the caller's array
-      auto kcb = k_copy_back_pass<K, HAS_V, sort_tile<K, HAS_V>()>;
+      auto kcb = k_copy_back_pass<K, HAS_V, (kBlock * IPT)>;
       HS_TRY(lc.kernel("copy_back_pass", kcb, 2 * 152, 256, 0, keys, vals, kw, vw, L.npk, o.stop_after - 2,
                        tb));
     }
@@ -375,20 +437,28 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
   return HS_OK;
 }
 
-template <class K>
-hs_status run_sort(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
-                   char* ws, uint32_t* err, cudaStream_t st) {
+// One sort call with the tile shape IPT (hs_opts.tile resolved by the
+// caller): values or not, then the partition variant.  Instantiated in one
+// translation unit per (key type, IPT) (sort_shape.cu).
+template <class K, bool HAS_V, int IPT>
+hs_status run_sort_part(K* k, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
+                        char* ws, uint32_t* err, cudaStream_t st) {
+  if (o.partition == 1) return run_sort_nb<K, HAS_V, 1, IPT>(k, vals, n, nseg, offs, o, ws, err, st);
+  if (o.partition == 256) return run_sort_nb<K, HAS_V, 256, IPT>(k, vals, n, nseg, offs, o, ws, err, st);
+  return run_sort_nb<K, HAS_V, 10, IPT>(k, vals, n, nseg, offs, o, ws, err, st);
+}
+
+template <class K, int IPT>
+hs_status run_sort_ipt(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
+                       char* ws, uint32_t* err, cudaStream_t st) {
   K* k = static_cast<K*>(keys);
-  if (o.partition == 1) {
-    if (vals) return run_sort_nb<K, true, 1>(k, vals, n, nseg, offs, o, ws, err, st);
-    return run_sort_nb<K, false, 1>(k, vals, n, nseg, offs, o, ws, err, st);
+  if (vals) {
+    if constexpr (ipt_built<K, true, IPT>()) return run_sort_part<K, true, IPT>(k, vals, n, nseg, offs, o, ws, err, st);
+    else return HS_ERR_UNSUPPORTED;
+  } else {
+    if constexpr (ipt_built<K, false, IPT>()) return run_sort_part<K, false, IPT>(k, vals, n, nseg, offs, o, ws, err, st);
+    else return HS_ERR_UNSUPPORTED;
   }
-  if (o.partition == 256) {
-    if (vals) return run_sort_nb<K, true, 256>(k, vals, n, nseg, offs, o, ws, err, st);
-    return run_sort_nb<K, false, 256>(k, vals, n, nseg, offs, o, ws, err, st);
-  }
-  if (vals) return run_sort_nb<K, true, 10>(k, vals, n, nseg, offs, o, ws, err, st);
-  return run_sort_nb<K, false, 10>(k, vals, n, nseg, offs, o, ws, err, st);
 }
 
 }  // namespace hs

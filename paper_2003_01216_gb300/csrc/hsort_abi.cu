@@ -52,14 +52,14 @@ struct GraphKey {
   uint32_t* vals;
   const uint64_t* offs;
   size_t n, nseg;
-  int partition, stop_after, debug, fan_in;
+  int partition, stop_after, debug, fan_in, tile;
   uint64_t* pkt_out;
   void* ws;
   size_t ws_bytes;
   bool operator<(const GraphKey& o) const {
-    return std::tie(dev, st, dtype, keys, vals, offs, n, nseg, partition, stop_after, debug, fan_in, pkt_out, ws,
+    return std::tie(dev, st, dtype, keys, vals, offs, n, nseg, partition, stop_after, debug, fan_in, tile, pkt_out, ws,
                     ws_bytes) < std::tie(o.dev, o.st, o.dtype, o.keys, o.vals, o.offs, o.n, o.nseg, o.partition,
-                                         o.stop_after, o.debug, o.fan_in, o.pkt_out, o.ws, o.ws_bytes);
+                                         o.stop_after, o.debug, o.fan_in, o.tile, o.pkt_out, o.ws, o.ws_bytes);
   }
 };
 struct GraphEntry {
@@ -130,7 +130,11 @@ struct TuneKey {
     return std::tie(dtype, has_vals, partition, log2n) < std::tie(o.dtype, o.has_vals, o.partition, o.log2n);
   }
 };
-std::map<TuneKey, int> g_tune;
+// value: the fan-in and the tile of the shape (0 = the built-in rule's)
+struct TuneVal {
+  int fan_in = 0, tile = 0;
+};
+std::map<TuneKey, TuneVal> g_tune;
 std::mutex g_tune_mu;
 
 int size_bucket(size_t n) {
@@ -138,15 +142,55 @@ int size_bucket(size_t n) {
   while (b < 63 && (static_cast<size_t>(1) << b) < n) ++b;
   return b;
 }
-int tuned_fan_in(int dtype, bool has_vals, int partition, size_t n) {
+// The shape a call with fan_in == 0 / tile == 0 uses: the tuning table's
+// entry for its (key type, values, partition, size bucket), else the built-in
+// rule from one GB300: four-way passes while passes are short (launch- and
+// latency-bound), two-way passes above 2^21 keys; the default tile.
+void tuned_shape(int dtype, bool has_vals, int partition, size_t n, int* fan_in, int* tile) {
+  TuneVal v;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(TuneKey{dtype, has_vals ? 1 : 0, partition, size_bucket(n)});
-    if (it != g_tune.end()) return it->second;
+    if (it != g_tune.end()) v = it->second;
   }
-  // built-in rule from one GB300: four-way passes win while passes are short
-  // (launch- and latency-bound), two-way passes above 2^21 keys
-  return n <= (static_cast<size_t>(1) << 21) ? 4 : 2;
+  if (fan_in) *fan_in = v.fan_in ? v.fan_in : (n <= (static_cast<size_t>(1) << 21) ? 4 : 2);
+  if (tile) *tile = v.tile ? v.tile : sort_tile_for(dtype == HS_UINT64 ? 8 : 4, has_vals);
+}
+int tuned_fan_in(int dtype, bool has_vals, int partition, size_t n) {
+  int f = 0;
+  tuned_shape(dtype, has_vals, partition, n, &f, nullptr);
+  return f;
+}
+
+// The per-(key type, tile shape) entry points of sort_shape.cu.
+hs_status run_shape(hs_dtype dt, int tile, void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs,
+                    const hs_opts& o, char* ws, uint32_t* err, cudaStream_t st) {
+  const int ipt = tile / kBlock;
+  switch (dt) {
+    case HS_INT32:
+      switch (ipt) {
+        case 11: return run_sort_i32_t11(keys, vals, n, nseg, offs, o, ws, err, st);
+        case 15: return run_sort_i32_t15(keys, vals, n, nseg, offs, o, ws, err, st);
+        case 23: return run_sort_i32_t23(keys, vals, n, nseg, offs, o, ws, err, st);
+        case 31: return run_sort_i32_t31(keys, vals, n, nseg, offs, o, ws, err, st);
+      }
+      break;
+    case HS_UINT32:
+      switch (ipt) {
+        case 11: return run_sort_u32_t11(keys, vals, n, nseg, offs, o, ws, err, st);
+        case 15: return run_sort_u32_t15(keys, vals, n, nseg, offs, o, ws, err, st);
+        case 23: return run_sort_u32_t23(keys, vals, n, nseg, offs, o, ws, err, st);
+        case 31: return run_sort_u32_t31(keys, vals, n, nseg, offs, o, ws, err, st);
+      }
+      break;
+    default:
+      switch (ipt) {
+        case 11: return run_sort_u64_t11(keys, vals, n, nseg, offs, o, ws, err, st);
+        case 15: return run_sort_u64_t15(keys, vals, n, nseg, offs, o, ws, err, st);
+      }
+      break;
+  }
+  return HS_ERR_UNSUPPORTED;
 }
 
 hs_status check_opts(const hs_opts* opts, hs_opts* o) {
@@ -154,7 +198,7 @@ hs_status check_opts(const hs_opts* opts, hs_opts* o) {
   if (opts) d = *opts;
   if (d.partition == 0) d.partition = 10;
   if (d.partition != 1 && d.partition != 10 && d.partition != 256) return HS_ERR_INVALID;
-  if (d.tile != 0 && d.tile != kBlock * 15 && d.tile != kBlock * 31) return HS_ERR_UNSUPPORTED;
+  if (d.tile != 0 && !tile_built(4, false, d.tile) && !tile_built(4, true, d.tile)) return HS_ERR_UNSUPPORTED;
   if (d.fan_in != 0 && d.fan_in != 2 && d.fan_in != 4) return HS_ERR_UNSUPPORTED;
   if (d.stop_after < 0 || d.stop_after > 2 + kMaxPasses) return HS_ERR_INVALID;
   *o = d;
@@ -172,8 +216,13 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
   if ((reinterpret_cast<uintptr_t>(keys) % key_bytes(dt)) || (reinterpret_cast<uintptr_t>(vals) & 3u) ||
       (reinterpret_cast<uintptr_t>(offs) & 7u))
     return HS_ERR_INVALID;
-  if (o.fan_in == 0) o.fan_in = tuned_fan_in(static_cast<int>(dt), vals != nullptr, o.partition, n);
-  if (o.tile != 0 && o.tile != sort_tile_for(key_bytes(dt), vals != nullptr)) return HS_ERR_UNSUPPORTED;
+  if (o.tile != 0 && !tile_built(key_bytes(dt), vals != nullptr, o.tile)) return HS_ERR_UNSUPPORTED;
+  {
+    int f = 0, t = 0;
+    tuned_shape(static_cast<int>(dt), vals != nullptr, o.partition, n, &f, &t);
+    if (o.fan_in == 0) o.fan_in = f;
+    if (o.tile == 0) o.tile = t;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (n == 0 && !offs) {
     if (o.d_packet_offsets_out) {
@@ -198,14 +247,12 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
   }
   auto run = [&]() -> hs_status {
     switch (dt) {
-      case HS_INT32: return run_sort_i32(keys, vals, n, nseg, offs, o, ws, err, st);
-      case HS_UINT32: return run_sort_u32(keys, vals, n, nseg, offs, o, ws, err, st);
-      default: return run_sort_u64(keys, vals, n, nseg, offs, o, ws, err, st);
+      default: return run_shape(dt, o.tile, keys, vals, n, nseg, offs, o, ws, err, st);
     }
   };
   if (!o.graph || st == nullptr || timing_on()) return run();
   const GraphKey key{current_device(), st, static_cast<int>(dt), keys, vals, offs, n, nseg, o.partition,
-                     o.stop_after, o.debug_flags, o.fan_in, o.d_packet_offsets_out, ws,
+                     o.stop_after, o.debug_flags, o.fan_in, o.tile, o.d_packet_offsets_out, ws,
                      o.d_workspace ? o.workspace_bytes : need};
   auto it = g_graphs.find(key);
   if (it == g_graphs.end()) {
@@ -366,7 +413,40 @@ hs_status hs_tune_set(hs_dtype dtype, int has_vals, int partition, int log2n, in
   if (partition != 1 && partition != 10 && partition != 256) return HS_ERR_INVALID;
   if (log2n < 0 || log2n > 32 || (fan_in != 2 && fan_in != 4)) return HS_ERR_INVALID;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[TuneKey{static_cast<int>(dtype), has_vals ? 1 : 0, partition, log2n}] = fan_in;
+  g_tune[TuneKey{static_cast<int>(dtype), has_vals ? 1 : 0, partition, log2n}].fan_in = fan_in;
+  return HS_OK;
+}
+
+hs_status hs_tune_set_shape(hs_dtype dtype, int has_vals, int partition, int log2n, int fan_in, int tile) {
+  if (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64) return HS_ERR_INVALID;
+  if (partition != 1 && partition != 10 && partition != 256) return HS_ERR_INVALID;
+  if (log2n < 0 || log2n > 32 || (fan_in != 0 && fan_in != 2 && fan_in != 4)) return HS_ERR_INVALID;
+  if (tile != 0 && !tile_built(key_bytes(dtype), has_vals != 0, tile)) return HS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  TuneVal& v = g_tune[TuneKey{static_cast<int>(dtype), has_vals ? 1 : 0, partition, log2n}];
+  v.fan_in = fan_in;
+  v.tile = tile;
+  return HS_OK;
+}
+
+hs_status hs_tune_get_shape(hs_dtype dtype, int has_vals, int partition, size_t n, int* fan_in, int* tile) {
+  if (!fan_in || !tile || (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64)) return HS_ERR_INVALID;
+  if (partition == 0) partition = 10;
+  if (partition != 1 && partition != 10 && partition != 256) return HS_ERR_INVALID;
+  tuned_shape(static_cast<int>(dtype), has_vals != 0, partition, n, fan_in, tile);
+  return HS_OK;
+}
+
+hs_status hs_tiles(hs_dtype dtype, int has_vals, int* tiles, int max, int* count) {
+  if (!count || (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64) || (max > 0 && !tiles))
+    return HS_ERR_INVALID;
+  int c = 0;
+  for (int ipt : kTileIpts) {
+    if (!tile_built(key_bytes(dtype), has_vals != 0, kBlock * ipt)) continue;
+    if (c < max) tiles[c] = kBlock * ipt;
+    ++c;
+  }
+  *count = c;
   return HS_OK;
 }
 
@@ -420,9 +500,15 @@ hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, 
   if (!out || (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64)) return HS_ERR_INVALID;
   hs_opts o;
   HS_TRY(check_opts(opts, &o));
-  out->tile = sort_tile_for(key_bytes(dtype), has_vals != 0);
+  if (o.tile != 0 && !tile_built(key_bytes(dtype), has_vals != 0, o.tile)) return HS_ERR_UNSUPPORTED;
+  {
+    int f = 0, t = 0;
+    tuned_shape(static_cast<int>(dtype), has_vals != 0, o.partition, n, &f, &t);
+    if (o.fan_in == 0) o.fan_in = f;
+    if (o.tile == 0) o.tile = t;
+  }
+  out->tile = o.tile;
   out->part_tile = kTile;
-  if (o.fan_in == 0) o.fan_in = tuned_fan_in(static_cast<int>(dtype), has_vals != 0, o.partition, n);
   out->fan_in = o.fan_in;
   out->merge_passes = (n == 0) ? 0 : worst_passes(n, static_cast<size_t>(out->tile), o.fan_in);
   // seg_plan, hist (x2 for int32), finalize, fold, 3 scan kernels, pkt, scan_units, scatter,
@@ -433,9 +519,16 @@ hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, 
                      static_cast<uint64_t>(L.npk) <= kPlanSmallEntries;
   const int plan_kernels = small ? 1 : (o.partition == 1 ? 2 : 7);
   int l = (o.partition == 1) ? 1 + plan_kernels : 1 + (dtype == HS_INT32 ? 2 : 1) + plan_kernels + 1;
+  // one short array (at most a tile) skips the packet-step kernels: the tile
+  // sort launch sorts it whole
+  if (o.stop_after == 0 && (nseg ? nseg : 1) == 1 && n <= static_cast<size_t>(out->tile)) l = 1 + plan_kernels;
   if (o.stop_after != 1) l += 1;
-  if (o.stop_after == 0) l += 2 * out->merge_passes;
-  if (o.stop_after >= 3) l += 2 * std::min(out->merge_passes, o.stop_after - 2) + 1;
+  // fan-in 2: every merge pass in one persistent launch; fan-in 4 (and the
+  // per-pass ablation, debug flag 4): two launches per pass
+  const bool sched = o.fan_in == 2 && !(o.debug_flags & 4);
+  auto merge_launches = [&](int p) { return p == 0 ? 0 : (sched ? 1 : 2 * p); };
+  if (o.stop_after == 0) l += merge_launches(out->merge_passes);
+  if (o.stop_after >= 3) l += merge_launches(std::min(out->merge_passes, o.stop_after - 2)) + 1;
   out->launches = (n == 0) ? 0 : l;
   return HS_OK;
 }

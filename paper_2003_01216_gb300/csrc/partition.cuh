@@ -42,18 +42,62 @@ namespace hs {
 // [0, n)).  Batches pass the caller's offsets, which are validated here; if
 // they are malformed every segment is treated as empty (no key moves) and the
 // error word gets kErrBadOffsets.
+//
+// Short segments (1 .. small_max keys; small_max = 0 turns this off) skip the
+// packet step, the tile sort of packets and the merges: one CTA of the tile
+// sort launch sorts each of them whole and writes its packet offsets (see
+// k_tilesort).  They get no packet-step blocks, so the (segment, packet,
+// block) scan counts only the other segments' keys; small_before[s] (keys of
+// short segments before s) turns its positions back into absolute ones, and
+// small_list holds the short segments in order (small_cnt of them).
 // ---------------------------------------------------------------------------
+// Block-wide exclusive scan of three counters at once (all threads call it);
+// returns the exclusive prefixes and writes the block totals to tot.
+__device__ __forceinline__ void block_scan3(uint32_t (&v)[3], uint32_t (&excl)[3], uint32_t (&tot)[3],
+                                            uint32_t (*s_warp)[32]) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  uint32_t inc[3] = {v[0], v[1], v[2]};
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, inc[q], o);
+      if (lane >= o) inc[q] += x;
+    }
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s_warp[q][wid] = inc[q];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      uint32_t w = (lane < nw) ? s_warp[q][lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += x;
+      }
+      s_warp[q][lane] = w;  // inclusive over warps
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    excl[q] = inc[q] - v[q] + (wid ? s_warp[q][wid - 1] : 0u);
+    tot[q] = s_warp[q][31];
+  }
+  __syncthreads();  // s_warp is reused by the next call
+}
+
 static __global__ void k_seg_plan(const uint64_t* __restrict__ offs, uint32_t nseg, uint64_t n, uint32_t part_tile,
-                           Tables tb) {
+                                  uint32_t small_max, Tables tb) {
   griddep_open();
   __shared__ uint32_t s_bad;
-  __shared__ uint32_t s_carry;
-  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_warp[3][32];
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    s_bad = 0;
-    s_carry = 0;
-  }
+  if (tid == 0) s_bad = 0;
   __syncthreads();
   if (offs) {
     for (uint32_t s = tid; s < nseg; s += nt)
@@ -63,46 +107,41 @@ static __global__ void k_seg_plan(const uint64_t* __restrict__ offs, uint32_t ns
   __syncthreads();
   const bool bad = s_bad != 0;
   if (bad && tid == 0) atomicOr(tb.err, kErrBadOffsets);
+  uint32_t carry[3] = {0, 0, 0};  // blocks, short-segment keys, short segments
   for (uint32_t base = 0; base <= nseg; base += nt) {
-    uint32_t s = base + tid;
-    uint64_t lo = 0, hi = 0;
+    const uint32_t s = base + tid;
     if (s <= nseg) {
-      uint64_t so = offs ? offs[s] : (s == 0 ? 0 : n);
+      const uint64_t so = offs ? offs[s] : (s == 0 ? 0 : n);
       tb.seg_off[s] = bad ? 0 : so;
     }
-    uint32_t nblk = 0;
+    uint32_t v[3] = {0, 0, 0};
     if (s < nseg && !bad) {
-      lo = offs ? offs[s] : 0;
-      hi = offs ? offs[s + 1] : n;
-      nblk = static_cast<uint32_t>((hi - lo + part_tile - 1) / part_tile);
-    }
-    // block-wide exclusive scan of nblk
-    uint32_t v = nblk;
-    const int lane = tid & 31, wid = tid >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t x = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += x;
-    }
-    if (lane == 31) s_warp[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-      uint32_t w = (lane < (nt >> 5)) ? s_warp[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t x = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += x;
+      const uint64_t lo = offs ? offs[s] : 0;
+      const uint64_t hi = offs ? offs[s + 1] : n;
+      const uint64_t len = hi - lo;
+      if (len > 0 && len <= small_max) {
+        v[1] = static_cast<uint32_t>(len);
+        v[2] = 1;
+      } else {
+        v[0] = static_cast<uint32_t>((len + part_tile - 1) / part_tile);
       }
-      s_warp[lane] = w;  // inclusive over warps
     }
-    __syncthreads();
-    uint32_t incl = v + (wid ? s_warp[wid - 1] : 0);
-    uint32_t carry = s_carry;
-    if (s <= nseg) tb.blk_prefix[s] = carry + incl - nblk;
-    __syncthreads();
-    if (tid == nt - 1) s_carry = carry + incl;
-    __syncthreads();
+    uint32_t ex[3], tot[3];
+    block_scan3(v, ex, tot, s_warp);
+    if (s <= nseg) {
+      tb.blk_prefix[s] = carry[0] + ex[0];
+      tb.small_before[s] = carry[1] + ex[1];
+    }
+    if (v[2]) tb.small_list[carry[2] + ex[2]] = s;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) carry[q] += tot[q];
   }
+  if (tid == 0) *tb.small_cnt = carry[2];
+}
+
+// A segment that skips the packet step: keys, but no packet-step blocks.
+__device__ __forceinline__ bool seg_is_small(const Tables& tb, uint32_t s) {
+  return tb.seg_off[s + 1] > tb.seg_off[s] && tb.blk_prefix[s + 1] == tb.blk_prefix[s];
 }
 
 // Locate the segment of packet-step block b (blk_prefix is non-decreasing).
@@ -352,10 +391,13 @@ __global__ void k_pkt(uint32_t nseg, uint32_t tile, Tables tb) {
        idx += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
     const uint32_t s = static_cast<uint32_t>(idx / NB), p = static_cast<uint32_t>(idx % NB);
     const uint32_t first = tb.blk_prefix[s], nb_s = tb.blk_prefix[s + 1] - first;
-    const uint64_t start = nb_s ? tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s]
+    const uint64_t sb = tb.small_before[s];
+    // a segment without blocks (empty or short) has no tiles here
+    const uint64_t start = nb_s ? sb + tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s]
                                 : tb.seg_off[s];
-    const uint64_t end = (nb_s && p + 1 < NB) ? tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p + 1) * nb_s]
-                                                : tb.seg_off[s + 1];
+    const uint64_t end = !nb_s ? tb.seg_off[s]
+                               : (p + 1 < NB) ? sb + tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p + 1) * nb_s]
+                                              : tb.seg_off[s + 1];
     tb.pkt_off[idx] = start;
     const uint32_t tiles = static_cast<uint32_t>((end - start + tile - 1) / tile);
     tb.unit_prefix[idx] = tiles;
@@ -373,7 +415,7 @@ __global__ void k_pkt(uint32_t nseg, uint32_t tile, Tables tb) {
 static __global__ void k_pkt_whole(uint32_t nseg, uint32_t tile, Tables tb) {
   griddep_open();
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
-    const uint64_t start = tb.seg_off[s], end = tb.seg_off[s + 1];
+    const uint64_t start = tb.seg_off[s], end = seg_is_small(tb, s) ? start : tb.seg_off[s + 1];
     tb.pkt_off[s] = start;
     const uint32_t tiles = static_cast<uint32_t>((end - start + tile - 1) / tile);
     tb.unit_prefix[s] = tiles;
@@ -525,7 +567,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_small(uint32_t nseg, uint
   const uint32_t m = nseg * NB;
   if constexpr (NB == 1) {
     for (uint32_t s = tid; s < nseg; s += nt) {
-      const uint64_t start = tb.seg_off[s], end = tb.seg_off[s + 1];
+      const uint64_t start = tb.seg_off[s], end = seg_is_small(tb, s) ? start : tb.seg_off[s + 1];
       tb.pkt_off[s] = start;
       const uint32_t tiles = static_cast<uint32_t>((end - start + tile - 1) / tile);
       tb.unit_prefix[s] = tiles;
@@ -622,11 +664,13 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_small(uint32_t nseg, uint
     for (uint32_t idx = tid; idx < m; idx += nt) {
       const uint32_t s = idx / NB, p = idx % NB;
       const uint32_t first = tb.blk_prefix[s], nb_s = tb.blk_prefix[s + 1] - first;
-      const uint64_t start = nb_s ? tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s]
+      const uint64_t sb = tb.small_before[s];
+      const uint64_t start = nb_s ? sb + tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s]
                                   : tb.seg_off[s];
-      const uint64_t end = (nb_s && p + 1 < NB)
-                               ? tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p + 1) * nb_s]
-                               : tb.seg_off[s + 1];
+      const uint64_t end = !nb_s ? tb.seg_off[s]
+                                 : (p + 1 < NB)
+                                       ? sb + tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p + 1) * nb_s]
+                                       : tb.seg_off[s + 1];
       tb.pkt_off[idx] = start;
       const uint32_t tiles = static_cast<uint32_t>((end - start + tile - 1) / tile);
       tb.unit_prefix[idx] = tiles;
@@ -679,7 +723,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_scatter(const K* __restrict__ keys
   const DigitRule rule = (NB == 10) ? rule_dec(cls) : make_rule_bin(cls);
   // absolute first position of this block's keys in every packet
   for (int p = tid; p < NB; p += BLOCK) {
-    s_gb[p] = tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s + (b - first)];
+    s_gb[p] = tb.small_before[seg] + tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(p) * nb_s + (b - first)];
     s_pe[p] = static_cast<uint32_t>(tb.pkt_off[static_cast<size_t>(seg) * NB + p + 1]);
   }
   __syncthreads();
@@ -853,7 +897,7 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_sc
   auto load_dst = [&](uint32_t bb, uint32_t& d, uint32_t& e) {
     const uint32_t sg = find_seg(tb.blk_prefix, nseg, bb);
     const uint32_t first = tb.blk_prefix[sg], nb_s = tb.blk_prefix[sg + 1] - first;
-    d = tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(tid) * nb_s + (bb - first)];
+    d = tb.small_before[sg] + tb.flat[static_cast<size_t>(first) * NB + static_cast<size_t>(tid) * nb_s + (bb - first)];
     e = static_cast<uint32_t>(tb.pkt_off[static_cast<size_t>(sg) * NB + tid + 1]);
   };
 

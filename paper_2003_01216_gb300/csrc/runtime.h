@@ -109,13 +109,21 @@ class Launcher {
   bool prev_kernel_ = false;
 };
 
-// Entry points of the per-key-type translation units.
-hs_status run_sort_i32(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
-                       char* ws, uint32_t* err, cudaStream_t st);
-hs_status run_sort_u32(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
-                       char* ws, uint32_t* err, cudaStream_t st);
-hs_status run_sort_u64(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
-                       char* ws, uint32_t* err, cudaStream_t st);
+// Entry points of the per-(key type, tile shape) translation units
+// (sort_shape.cu): run_sort_<key>_t<items per thread>.
+#define HS_SORT_SHAPE_DECL(name)                                                                            \
+  hs_status name(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o, \
+                 char* ws, uint32_t* err, cudaStream_t st)
+HS_SORT_SHAPE_DECL(run_sort_i32_t11);
+HS_SORT_SHAPE_DECL(run_sort_i32_t15);
+HS_SORT_SHAPE_DECL(run_sort_i32_t23);
+HS_SORT_SHAPE_DECL(run_sort_i32_t31);
+HS_SORT_SHAPE_DECL(run_sort_u32_t11);
+HS_SORT_SHAPE_DECL(run_sort_u32_t15);
+HS_SORT_SHAPE_DECL(run_sort_u32_t23);
+HS_SORT_SHAPE_DECL(run_sort_u32_t31);
+HS_SORT_SHAPE_DECL(run_sort_u64_t11);
+HS_SORT_SHAPE_DECL(run_sort_u64_t15);
 size_t workspace_bytes(size_t key_bytes, size_t n, bool has_vals, size_t nseg, int nb);
 
 }  // namespace hs

@@ -17,8 +17,36 @@ __device__ __forceinline__ int levels_for(int cnt) {
   return lv;
 }
 
-template <class K, bool HAS_V, int BLOCK, int IPT>
-__global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, const uint32_t* __restrict__ vw, K* ku,
+// Packet offsets of a short segment sorted whole (see k_seg_plan): the
+// segment's class follows from its smallest key (a negative int32 key means
+// the flipped image) and its largest; in sorted order the packets are
+// contiguous, so the item at position i opens every packet in
+// (packet of item i-1, packet of item i].  The staged region `st` holds all
+// cnt sorted keys; each thread reads its own items (blocked, conflict-free).
+template <class K, int NB, int IPT>
+__device__ __forceinline__ void short_segment_offsets(const K* st, int cnt, uint64_t beg, uint64_t* po) {
+  using U = typename KT<K>::U;
+  const bool flip = KT<K>::negative(st[0]);
+  const U umax = KT<K>::image(st[cnt - 1], flip);
+  const int cls = (NB == 10) ? dec_class(umax) : bin_class(umax);
+  const DigitRule rule = (NB == 10) ? rule_dec(cls) : make_rule_bin(cls);
+  const int i0 = static_cast<int>(threadIdx.x) * IPT;
+  int qp = (i0 == 0 || i0 >= cnt) ? -1 : static_cast<int>(packet_of<NB>(KT<K>::image(st[i0 - 1], flip), rule));
+#pragma unroll 1
+  for (int i = i0; i < min(i0 + IPT, cnt); ++i) {
+    const int q = static_cast<int>(packet_of<NB>(KT<K>::image(st[i], flip), rule));
+    for (int p = qp + 1; p <= q; ++p) po[p] = beg + static_cast<uint64_t>(i);
+    if (i == cnt - 1)
+      for (int p = q + 1; p < NB; ++p) po[p] = beg + static_cast<uint64_t>(cnt);
+    qp = q;
+  }
+}
+
+// Work items of one launch: first every tile of every packet (read from the
+// packet layout, written to U or W), then every short segment (read from and
+// written back to the caller's array, its packet offsets written too).
+template <class K, bool HAS_V, int NB, int BLOCK, int IPT>
+__global__ void __launch_bounds__(BLOCK, (sizeof(K) == 4 && !HAS_V) ? 5 : 4) k_tilesort(const K* __restrict__ kw, const uint32_t* __restrict__ vw, K* ku,
                                                      uint32_t* vu, K* kw_out, uint32_t* vw_out, uint32_t npk,
                                                      int force_w, int debug_stuck, uint64_t limit_ns, Tables tb) {
   griddep_open();
@@ -30,21 +58,42 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
   __shared__ __align__(8) uint64_t s_bar;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t total = tb.unit_prefix[npk];
+  const uint32_t items = total + *tb.small_cnt;
   if (tid == 0) mbar_init(&s_bar, 1);
   mbar_fence_init();
   __syncthreads();
   uint32_t parity = 0;
   bool failed = false;
 
-  for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
-    const uint32_t p = find_pkt(tb.unit_prefix, npk, u);
-    const uint32_t up0 = tb.unit_prefix[p], ntiles = tb.unit_prefix[p + 1] - up0;
-    const int passes = passes_of(ntiles, tb.fan_log2);
-    const bool to_w = force_w || (passes & 1);
-    const uint64_t beg = tb.pkt_off[p] + static_cast<uint64_t>(u - up0) * TILE;
-    const int cnt = static_cast<int>(min64(TILE, tb.pkt_off[p + 1] - beg));
-    const K* gk = kw + beg;
-    const uint32_t* gv = HAS_V ? vw + beg : nullptr;
+  for (uint32_t u = blockIdx.x; u < items; u += gridDim.x) {
+    const bool short_seg = u >= total;
+    uint32_t seg = 0;
+    uint64_t beg;
+    int cnt;
+    const K* gk;
+    const uint32_t* gv;
+    K* kd;
+    uint32_t* vd;
+    if (!short_seg) {
+      const uint32_t p = find_pkt(tb.unit_prefix, npk, u);
+      const uint32_t up0 = tb.unit_prefix[p], ntiles = tb.unit_prefix[p + 1] - up0;
+      const int passes = passes_of(ntiles, tb.fan_log2);
+      const bool to_w = force_w || (passes & 1);
+      beg = tb.pkt_off[p] + static_cast<uint64_t>(u - up0) * TILE;
+      cnt = static_cast<int>(min64(TILE, tb.pkt_off[p + 1] - beg));
+      gk = kw + beg;
+      gv = HAS_V ? vw + beg : nullptr;
+      kd = (to_w ? kw_out : ku) + beg;
+      vd = HAS_V ? (to_w ? vw_out : vu) + beg : nullptr;
+    } else {
+      seg = tb.small_list[u - total];
+      beg = tb.seg_off[seg];
+      cnt = static_cast<int>(min64(TILE, tb.seg_off[seg + 1] - beg));  // at most a tile by construction
+      gk = ku + beg;
+      gv = HAS_V ? vu + beg : nullptr;
+      kd = ku + beg;
+      vd = HAS_V ? vu + beg : nullptr;
+    }
     const uint32_t pk = phase_of(gk);
     const uint32_t pv = HAS_V ? phase_of(gv) : 0u;
 
@@ -115,8 +164,6 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
       }
     }
     // blocked registers -> region at the destination's phase -> bulk store
-    K* kd = (to_w ? kw_out : ku) + beg;
-    uint32_t* vd = HAS_V ? (to_w ? vw_out : vu) + beg : nullptr;
     const uint32_t ok_ph = phase_of(kd);
     const uint32_t ov_ph = HAS_V ? phase_of(vd) : 0u;
     __syncthreads();
@@ -134,6 +181,12 @@ __global__ void __launch_bounds__(BLOCK) k_tilesort(const K* __restrict__ kw, co
       store_window(kd, rk + ok_ph, cnt, lane);
       if constexpr (HAS_V) store_window(vd, rv + ov_ph, cnt, lane);
       if (lane == 0) bulk_commit();
+    }
+    if constexpr (NB > 1) {
+      if (short_seg) {  // block-uniform
+        short_segment_offsets<K, NB, IPT>(rk + ok_ph, cnt, beg, tb.pkt_off + static_cast<size_t>(seg) * NB);
+        __syncthreads();  // every read of the region is done before the next item's copy refills it
+      }
     }
   }
   // a copy may still be in flight into the region: give it a bounded chance

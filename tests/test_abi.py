@@ -90,15 +90,27 @@ def test_plan_describe(n):
         blocks = -(-n // 3840) + 1
         small = blocks * 10 <= 1 << 16
         hist = 2 if dtype == N.HS_INT32 else 1
-        assert p["launches"] == 1 + hist + (1 if small else 7) + 2 + 2 * passes
+        # an array of at most one tile is sorted whole by the tile sort launch:
+        # seg_plan, the one-CTA plan, tile sort
+        short = n <= tile
+        # fan-in 2: every merge pass in one persistent launch (the per-pass
+        # ablation, debug flag 4, takes a co-rank and a merge launch per pass)
+        sched = 1 if passes else 0
+        assert p["launches"] == (3 if short else 1 + hist + (1 if small else 7) + 2 + sched)
+        per_pass = hs.plan(dtype, n, has_vals, fan_in=2, debug_flags=4)["launches"]
+        assert per_pass == (3 if short else 1 + hist + (1 if small else 7) + 2 + 2 * passes)
         # without the MSD step: seg_plan, packet table, tile prefix, tile sort
         small1 = blocks <= 1 << 16
-        assert hs.plan(dtype, n, has_vals, partition=1, fan_in=2)["launches"] == (3 if small1 else 4) + 2 * passes
+        assert hs.plan(dtype, n, has_vals, partition=1, fan_in=2)["launches"] == (
+            3 if short else (3 if small1 else 4) + sched)
+        # the testing stop after the tile sort keeps the packet step
+        assert hs.plan(dtype, n, has_vals, fan_in=2, stop_after=2)["launches"] == (
+            1 + hist + (1 if small else 7) + 2)
         # fan-in 4: ceil(log4(tiles)) passes, still two launches each
         p4 = hs.plan(dtype, n, has_vals, fan_in=4)
         passes4 = 0 if tiles <= 1 else math.ceil(math.log(tiles, 4) - 1e-12)
         assert p4["fan_in"] == 4 and p4["merge_passes"] == passes4 == (passes + 1) // 2
-        assert p4["launches"] == 1 + hist + (1 if small else 7) + 2 + 2 * passes4
+        assert p4["launches"] == (3 if short else 1 + hist + (1 if small else 7) + 2 + 2 * passes4)
         assert p["fan_in"] == 2
 
 
@@ -107,8 +119,10 @@ def test_stop_after_merge_pass_plan():
     full = hs.plan(N.HS_INT32, 1 << 24, fan_in=2)
     for r in (1, 3, full["merge_passes"], full["merge_passes"] + 5):
         p = hs.plan(N.HS_INT32, 1 << 24, fan_in=2, stop_after=2 + r)
-        # the passes up to r, then one copy-back kernel
-        assert p["launches"] == full["launches"] - 2 * full["merge_passes"] + 2 * min(r, full["merge_passes"]) + 1
+        # the passes up to r (one scheduler launch), then one copy-back kernel
+        assert p["launches"] == full["launches"] + 1
+        q = hs.plan(N.HS_INT32, 1 << 24, fan_in=2, stop_after=2 + r, debug_flags=4)
+        assert q["launches"] == full["launches"] - 1 + 2 * min(r, full["merge_passes"]) + 1
     lib = N.lib()
     assert lib.hs_sort_keys(0, ctypes.c_void_p(0x1000), 10, ctypes.byref(N.make_opts(stop_after=67)), None) == \
         N.HS_ERR_INVALID
@@ -173,3 +187,36 @@ def test_tuning_cache_roundtrip(tmp_path):
         assert tune.size_bucket(1) == 0 and tune.size_bucket(1 << 20) == 20 and tune.size_bucket((1 << 20) + 1) == 21
     finally:
         tune.clear()
+
+
+def test_tile_shapes_and_tuning_table():
+    import paper_2003_01216_gb300 as hs
+    assert hs.tiles(N.HS_INT32) == [3840, 5888, 7936]
+    assert hs.tiles(N.HS_UINT64) == [2816, 3840] == hs.tiles(N.HS_INT32, True)
+    # a call's plan follows the tile asked for; the default is the largest 4-byte tile
+    for tile in hs.tiles(N.HS_INT32):
+        p = hs.plan(N.HS_INT32, 1 << 22, tile=tile, fan_in=2)
+        assert p["tile"] == tile
+        assert p["merge_passes"] == int(-(-(1 << 22) // tile) - 1).bit_length()
+    with pytest.raises(hs.HsError):
+        hs.plan(N.HS_UINT64, 1 << 20, tile=7936)
+    lib = N.lib()
+    fan, tile = ctypes.c_int(), ctypes.c_int()
+    lib.hs_tune_clear()
+    try:
+        assert lib.hs_tune_get_shape(0, 0, 10, 1 << 20, ctypes.byref(fan), ctypes.byref(tile)) == N.HS_OK
+        assert (fan.value, tile.value) == (4, 7936)  # the built-in rule
+        assert lib.hs_tune_set_shape(0, 0, 10, 20, 2, 3840) == N.HS_OK
+        assert lib.hs_tune_get_shape(0, 0, 10, 1 << 20, ctypes.byref(fan), ctypes.byref(tile)) == N.HS_OK
+        assert (fan.value, tile.value) == (2, 3840)
+        assert hs.plan(N.HS_INT32, 1 << 20)["tile"] == 3840  # tile = 0 takes the table's
+        assert hs.plan(N.HS_INT32, 1 << 21)["tile"] == 7936  # another size bucket
+        # the fan-in alone keeps the tuned tile
+        assert lib.hs_tune_set(0, 0, 10, 20, 4) == N.HS_OK
+        assert lib.hs_tune_get_shape(0, 0, 10, 1 << 20, ctypes.byref(fan), ctypes.byref(tile)) == N.HS_OK
+        assert (fan.value, tile.value) == (4, 3840)
+        # shapes not built for the key type are refused
+        assert lib.hs_tune_set_shape(2, 0, 10, 20, 2, 7936) == N.HS_ERR_INVALID
+        assert lib.hs_tune_set_shape(0, 0, 10, 20, 3, 3840) == N.HS_ERR_INVALID
+    finally:
+        lib.hs_tune_clear()

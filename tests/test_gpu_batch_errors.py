@@ -165,12 +165,56 @@ def test_autotune_installs_a_correct_choice(oracle):
     try:
         entries = tune.autotune(0, [1 << 16, 3 << 18], reps=2)
         assert [e["log2n"] for e in entries] == [16, 20]
+        shapes = [(f, t) for t in hs.tiles(0) for f in (2, 4)]
         for e in entries:
-            assert set(e["ms"]) == {"2", "4"} and e["fan_in"] == min((2, 4), key=lambda f: e["ms"][str(f)])
-            assert tune.get(0, 1 << e["log2n"]) == e["fan_in"]
+            assert set(e["ms"]) == {f"{f}x{t}" for f, t in shapes}
+            best = min(shapes, key=lambda ft: e["ms"][f"{ft[0]}x{ft[1]}"])
+            assert (e["fan_in"], e["tile"]) == best
+            assert tune.get_shape(0, 1 << e["log2n"]) == best
+            assert hs.plan(0, 1 << e["log2n"])["tile"] == e["tile"]
         keys = I.generate("zipf", 3 << 18, seed=44)
-        gk, _, _, st = run(keys)  # fan_in = 0: the tuned entry
+        gk, _, _, st = run(keys)  # fan_in = 0, tile = 0: the tuned entry
         assert st == 0
-        assert_equal(gk, oracle.sort(keys)[0], "sort with the tuned fan-in")
+        assert_equal(gk, oracle.sort(keys)[0], "sort with the tuned shape")
+        # every tile the tuner may install sorts correctly at this size
+        for f, t in shapes:
+            gk, _, _, st = run(keys, fan_in=f, tile=t)
+            assert st == 0
+            assert_equal(gk, oracle.sort(keys)[0], f"sort with fan-in {f}, tile {t}")
     finally:
         tune.clear()
+
+
+def test_merge_queue_wait_expires_and_context_survives(oracle):
+    # the merge passes run as one persistent queue; the first merge block of
+    # pass 1 never publishes its completion (debug flag 2) and the wait limit
+    # is 2 ms: the pass-2 blocks that read its run give up and the call
+    # reports HS_ERR_TIMEOUT
+    keys = I.generate("uniform31", 100_000, seed=15)  # two packets of ~6 tiles: three passes
+    assert hs.plan(0, keys.size, fan_in=2)["merge_passes"] >= 2
+    _, _, _, st = run(keys, debug_flags=2, fan_in=2)
+    assert st == HS_TIMEOUT
+    # the context stays usable and the next call is correct
+    gk, _, _, st = run(keys, fan_in=2)
+    assert st == 0
+    assert_equal(gk, oracle.sort(keys)[0], "sort after an expired merge-queue wait")
+
+
+@pytest.mark.parametrize("dist,n,with_vals", [("uniform31", 3_000_000, False), ("zipf", 1_500_000, True),
+                                              ("uniform64", 1_000_000, True), ("sorted", 2_000_000, False)])
+def test_merge_queue_equals_per_pass_launches(oracle, dist, n, with_vals):
+    # one persistent merge launch (default for fan-in 2) against one co-rank
+    # and one merge launch per pass (debug flag 4): the same bits, and the
+    # oracle's
+    keys = I.generate(dist, n, seed=16)
+    vals = I.index_values(n) if with_vals else None
+    a = run(keys, vals, fan_in=2)
+    b = run(keys, vals, fan_in=2, debug_flags=4)
+    assert a[3] == 0 and b[3] == 0
+    assert_equal(a[0], b[0], "keys: queue vs per-pass")
+    ek, ev, eo = oracle.sort(keys, vals)
+    assert_equal(a[0], ek, "keys")
+    assert_equal(a[2], eo, "packet offsets")
+    if with_vals:
+        assert_equal(a[1], b[1], "values: queue vs per-pass")
+        assert_equal(a[1], ev, "stable values")
