@@ -290,7 +290,7 @@ def workload_config(args, dist, n, has_vals, world=1):
     return {"workload": f"{args.workload}_{n}_{dist}_{args.partition}pkt", "n": n, "dist": dist,
             "key_dtype": "uint64" if dist in ("uniform64", "distinct2p24") else "int32",
             "values": "uint32 input index" if has_vals else None, "partition": args.partition,
-            "tile": tile, "fan_in": fan, "merge": getattr(args, "merge", "queue"), "seed": 0,
+            "tile": tile, "fan_in": fan, "merge": getattr(args, "merge", "auto"), "seed": 0,
             "parallelism": f"replicas{world}",
             "l2": "inputs larger than L2 (>= 1 GiB vs 129 MB); a 1 GiB restore copy between timed steps"}
 
@@ -308,8 +308,9 @@ def main():
     ap.add_argument("--partition", type=int, default=10)
     ap.add_argument("--fan-in", type=int, default=0, help="runs per merge pass: 2 or 4 (0 = library default)")
     ap.add_argument("--n", type=int, default=None)
-    ap.add_argument("--merge", default="queue", choices=["queue", "per_pass"],
-                    help="two-way merge passes as one persistent queue launch, or two launches per pass (ablation)")
+    ap.add_argument("--merge", default="auto", choices=["auto", "queue", "per_pass"],
+                    help="two-way merge passes as one persistent queue launch, or two launches per pass "
+                         "(auto = the library's choice)")
     ap.add_argument("--tile", type=int, default=0, help="keys per tile (0 = library default)")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--ref-sample", type=int, default=1 << 23)
@@ -363,7 +364,7 @@ def main():
     pkt = torch.zeros(args.partition + 1, dtype=torch.uint64, device=dev)
     stream = torch.cuda.current_stream()
 
-    dbg = 4 if args.merge == "per_pass" else 0
+    mrg = {"auto": 0, "queue": 1, "per_pass": 2}[args.merge]
 
     def restore():
         work.copy_(pristine)
@@ -375,10 +376,10 @@ def main():
         # them); the timed steps sort the way a caller without it would
         if has_vals:
             hs.sort_pairs(work, vals, partition=args.partition, packet_offsets=offsets, fan_in=args.fan_in,
-                          tile=args.tile, debug_flags=dbg)
+                          tile=args.tile, merge=mrg)
         else:
             hs.sort_keys(work, partition=args.partition, packet_offsets=offsets, fan_in=args.fan_in, tile=args.tile,
-                         debug_flags=dbg)
+                         merge=mrg)
 
     # warm-up (also sizes the work space outside the timed region; the last
     # one returns the packet offsets, identical for every step of one input)
@@ -527,7 +528,7 @@ def main():
 
 
 def batch_measure(dev, hi: int, steps: int, warmup: int, dist_name: str = "uniform31", world: int = 1,
-                  debug_flags: int = 0) -> dict:
+                  merge: int = 0) -> dict:
     """Config 4: 10,000 int32 segments, lengths log-uniform in [16, hi], sorted
     by one hs_sort_batch call (one CUDA-graph launch), against the plain sort
     looped over the segments on the same stream and data.  Returns the timing
@@ -547,7 +548,7 @@ def batch_measure(dev, hi: int, steps: int, warmup: int, dist_name: str = "unifo
     with torch.cuda.stream(st):
         for _ in range(warmup):
             work.copy_(pristine)
-            hs.sort_batch(work, offs, graph=True, debug_flags=debug_flags)
+            hs.sort_batch(work, offs, graph=True, merge=merge)
         if hs.stream_error(st) != 0:
             raise RuntimeError("device error during warm-up")
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -559,7 +560,7 @@ def batch_measure(dev, hi: int, steps: int, warmup: int, dist_name: str = "unifo
             for i in range(steps):
                 work.copy_(pristine)
                 ev[i][0].record(st)
-                hs.sort_batch(work, offs, graph=True, debug_flags=debug_flags)
+                hs.sort_batch(work, offs, graph=True, merge=merge)
                 ev[i][1].record(st)
             torch.cuda.synchronize()
             clk.done()
@@ -598,7 +599,7 @@ def run_batch(args, rank, world, dev, dist_name):
     """Batched sort (one CUDA-graph launch for all segments) against the plain
     sort looped over the segments, same stream, same data."""
     rec = batch_measure(dev, args.batch_hi, args.steps, args.warmup, dist_name, world,
-                        4 if args.merge == "per_pass" else 0)
+                        {"auto": 0, "queue": 1, "per_pass": 2}[args.merge])
     if rank == 0:
         print(json.dumps({
             "metric": "batched sort throughput (keys/s): one graph launch over all segments",

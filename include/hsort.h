@@ -93,13 +93,23 @@ typedef struct {
                            allocates nothing for this call */
   size_t workspace_bytes;
   int debug_flags;      /* testing only: bit 0 = one bulk copy announces 16 bytes that never
-                           arrive and the wait limit is shortened, so a bounded wait expires */
+                           arrive and the wait limit is shortened, so a bounded wait expires;
+                           bit 1 = in the persistent merge launch, the first merge block never
+                           publishes its completion and the wait limit is shortened, so the
+                           blocks that read its run give up (HS_ERR_TIMEOUT) */
   int graph;            /* 1 = capture this call's whole launch sequence in a CUDA graph the
                            first time these exact arguments (pointers, sizes, options, stream)
                            are seen, and replay the instantiated graph on later calls.  Needs a
                            created stream (the legacy default stream cannot be captured) and
                            per-kernel timing off; otherwise the call runs without a graph.  The
                            library keeps up to 64 graphs; hs_graph_cache_clear frees them. */
+  int merge;            /* how two-way merge passes are launched (the result is the same):
+                           1 = every pass in one persistent launch, a work queue of
+                           (packet, pass, merge block) items each started as soon as the runs
+                           it reads are complete; 2 = one co-rank and one merge launch per
+                           pass; 0 = tuned: the tuning table's entry, else 1 above 2^24 keys
+                           (64-bit keys without values) or 2^26 keys (otherwise) and 2 up to
+                           it.  Other values: HS_ERR_UNSUPPORTED */
 } hs_opts;
 
 /*
@@ -224,15 +234,18 @@ hs_status hs_tune_set(hs_dtype dtype, int has_vals, int partition, int log2n, in
 hs_status hs_tune_get(hs_dtype dtype, int has_vals, int partition, size_t n, int* fan_in);
 hs_status hs_tune_clear(void);
 
-/* Tuning table, whole shape: the merge fan-in (2, 4, or 0 = the built-in rule)
- * and the tile (a built tile of the key type, or 0 = the default tile) that
- * calls with opts->fan_in == 0 / opts->tile == 0 use for this (key type, has
+/* Tuning table, whole shape: the merge fan-in (2, 4, or 0 = the built-in rule),
+ * the tile (a built tile of the key type, or 0 = the default tile) and the
+ * merge launch style (1, 2, or 0 = the built-in rule; see hs_opts.merge) that
+ * calls with opts->fan_in / tile / merge == 0 use for this (key type, has
  * values, partition, size bucket = ceil(log2(n))).  The shape changes only how
  * the work is cut (tile sort, merge blocks, passes), never the result, which is
  * the sorted order of Sec. 3.4 bit for bit.  Invalid values: HS_ERR_INVALID.
  * hs_tune_get_shape: the shape a call for n keys would use. */
-hs_status hs_tune_set_shape(hs_dtype dtype, int has_vals, int partition, int log2n, int fan_in, int tile);
-hs_status hs_tune_get_shape(hs_dtype dtype, int has_vals, int partition, size_t n, int* fan_in, int* tile);
+hs_status hs_tune_set_shape(hs_dtype dtype, int has_vals, int partition, int log2n, int fan_in, int tile,
+                            int merge);
+hs_status hs_tune_get_shape(hs_dtype dtype, int has_vals, int partition, size_t n, int* fan_in, int* tile,
+                            int* merge);
 
 /* The tiles built for a key type (and values): writes up to `max` of them to
  * `tiles` (ascending) and their number to *count. */

@@ -45,7 +45,7 @@ def _check_dev(*ts):
             raise ValueError("tensor must be contiguous")
 
 
-def _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph=False, fan_in=0, tile=0):
+def _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph=False, fan_in=0, tile=0, merge=0):
     po = 0
     if packet_offsets is not None:
         _check_dev(packet_offsets)
@@ -55,29 +55,33 @@ def _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph=F
         _check_dev(workspace)
         wp, wb = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     return N.make_opts(partition=partition, stop_after=stop_after, packet_offsets_ptr=po, workspace_ptr=wp,
-                       workspace_bytes=wb, debug_flags=debug_flags, graph=graph, fan_in=fan_in, tile=tile)
+                       workspace_bytes=wb, debug_flags=debug_flags, graph=graph, fan_in=fan_in, tile=tile,
+                       merge=merge)
 
 
 def sort_keys(keys, partition: int = 10, stop_after: int = 0, packet_offsets=None, stream=None,
-              debug_flags: int = 0, workspace=None, graph: bool = False, fan_in: int = 0, tile: int = 0):
+              debug_flags: int = 0, workspace=None, graph: bool = False, fan_in: int = 0, tile: int = 0,
+              merge: int = 0):
     """Sort a CUDA tensor of int32/uint32/uint64 keys in place (ascending).
     fan_in: runs merged per merge pass, 2 or 4; tile: keys per tile, one of
-    tiles(dtype) (0 = the tuned or default shape)."""
+    tiles(dtype); merge: 1 = two-way passes in one persistent launch, 2 = a
+    launch per pass (0 everywhere = the tuned or default shape)."""
     _check_dev(keys)
-    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in, tile)
+    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in, tile, merge)
     N.check(N.lib().hs_sort_keys(dtype_code(keys), keys.data_ptr(), keys.numel(), ctypes.byref(o), _stream(stream)),
             "hs_sort_keys")
     return keys
 
 
 def sort_pairs(keys, vals, partition: int = 10, stop_after: int = 0, packet_offsets=None, stream=None,
-               debug_flags: int = 0, workspace=None, graph: bool = False, fan_in: int = 0, tile: int = 0):
+               debug_flags: int = 0, workspace=None, graph: bool = False, fan_in: int = 0, tile: int = 0,
+               merge: int = 0):
     """Stable in-place sort of (key, uint32 value) pairs by key."""
     import torch
     _check_dev(keys, vals)
     if vals.dtype not in (torch.uint32, torch.int32) or vals.numel() != keys.numel():
         raise ValueError("vals must be a uint32 (or int32) tensor as long as keys")
-    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in, tile)
+    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in, tile, merge)
     N.check(N.lib().hs_sort_pairs(dtype_code(keys), keys.data_ptr(), vals.data_ptr(), keys.numel(), 1,
                                   ctypes.byref(o), _stream(stream)), "hs_sort_pairs")
     return keys, vals
@@ -85,11 +89,11 @@ def sort_pairs(keys, vals, partition: int = 10, stop_after: int = 0, packet_offs
 
 def sort_batch(keys, offsets, vals=None, partition: int = 10, stop_after: int = 0, packet_offsets=None,
                stream=None, workspace=None, graph: bool = False, fan_in: int = 0, tile: int = 0,
-               debug_flags: int = 0):
+               debug_flags: int = 0, merge: int = 0):
     """Sort every segment [offsets[s], offsets[s+1]) of `keys` on its own.
     offsets: CUDA uint64 (or int64) tensor of nseg + 1 entries."""
     _check_dev(keys, offsets, vals)
-    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in, tile)
+    o = _opts(partition, stop_after, packet_offsets, debug_flags, workspace, graph, fan_in, tile, merge)
     nseg = offsets.numel() - 1
     vp = vals.data_ptr() if vals is not None else None
     N.check(N.lib().hs_sort_batch(dtype_code(keys), keys.data_ptr(), vp, offsets.data_ptr(), nseg, keys.numel(),
@@ -127,9 +131,10 @@ def tiles(dtype: int, has_vals: bool = False) -> list[int]:
 
 
 def plan(dtype: int, n: int, has_vals: bool = False, nseg: int = 1, partition: int = 10, stop_after: int = 0,
-         fan_in: int = 0, debug_flags: int = 0, tile: int = 0):
+         fan_in: int = 0, debug_flags: int = 0, tile: int = 0, merge: int = 0):
     p = N.HsPlan()
-    o = N.make_opts(partition=partition, stop_after=stop_after, fan_in=fan_in, debug_flags=debug_flags, tile=tile)
+    o = N.make_opts(partition=partition, stop_after=stop_after, fan_in=fan_in, debug_flags=debug_flags, tile=tile,
+                    merge=merge)
     N.check(N.lib().hs_plan_describe(dtype, n, int(has_vals), nseg, ctypes.byref(o), ctypes.byref(p)),
             "hs_plan_describe")
     return {"tile": p.tile, "part_tile": p.part_tile, "merge_passes": p.merge_passes, "launches": p.launches,

@@ -36,6 +36,7 @@ class HsOpts(ctypes.Structure):
         ("workspace_bytes", ctypes.c_size_t),
         ("debug_flags", ctypes.c_int),
         ("graph", ctypes.c_int),
+        ("merge", ctypes.c_int),
     ]
 
 
@@ -84,8 +85,8 @@ def lib() -> ctypes.CDLL:
         L.hs_tune_set.argtypes = [i, i, i, i, i]
         L.hs_tune_get.argtypes = [i, i, i, sz, p]
         L.hs_tune_clear.argtypes = []
-        L.hs_tune_set_shape.argtypes = [i, i, i, i, i, i]
-        L.hs_tune_get_shape.argtypes = [i, i, i, sz, p, p]
+        L.hs_tune_set_shape.argtypes = [i, i, i, i, i, i, i]
+        L.hs_tune_get_shape.argtypes = [i, i, i, sz, p, p, p]
         L.hs_tiles.argtypes = [i, i, p, i, p]
         L.hs_stream_error.argtypes = [p]
         L.hs_plan_describe.argtypes = [i, sz, i, sz, p, p]
@@ -120,6 +121,6 @@ def check(status: int, where: str) -> None:
 
 def make_opts(partition: int = 10, stop_after: int = 0, packet_offsets_ptr: int = 0, workspace_ptr: int = 0,
               workspace_bytes: int = 0, debug_flags: int = 0, tile: int = 0, fan_in: int = 0,
-              graph: bool = False) -> HsOpts:
+              graph: bool = False, merge: int = 0) -> HsOpts:
     return HsOpts(partition, tile, fan_in, stop_after, packet_offsets_ptr or None, workspace_ptr or None,
-                  workspace_bytes, debug_flags, int(graph))
+                  workspace_bytes, debug_flags, int(graph), merge)

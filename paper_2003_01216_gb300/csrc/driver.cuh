@@ -56,6 +56,8 @@ inline int min_tile_for(size_t key_bytes, bool has_vals) {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 constexpr int kMaxPasses = 64;
+constexpr int kMergeQueue = 1;    // hs_opts.merge: every two-way pass in one persistent launch
+constexpr int kMergePerPass = 2;  // hs_opts.merge: a co-rank and a merge launch per pass
 // Lanes per co-rank search: more lanes per search when a pass has few merge
 // blocks (its co-rank kernel is then bound by the latency of the search
 // chain), one thread per merge block when it has many.
@@ -263,7 +265,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
   // zero the per-segment flags and maxima and the pass control (one region)
   HS_TRY(lc.memset("zero_tables", ws + L.zero, 0, L.zero_bytes));
   // the merge scheduler's ticket and completion counters
-  const bool use_sched = fan == 2 && !(o.debug_flags & 4) && o.stop_after != 1 && o.stop_after != 2 &&
+  const bool use_sched = fan == 2 && o.merge != kMergePerPass && o.stop_after != 1 && o.stop_after != 2 &&
                          worst_passes(n, (kBlock * IPT)) > 0;
   if (use_sched) HS_TRY(lc.memset("zero_sched", ws + L.sched, 0, L.sched_bytes));
   const bool small = static_cast<uint64_t>(L.max_blocks) * NB <= kPlanSmallEntries &&
@@ -390,7 +392,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
         HS_TRY(lc.kernel("merge4", mk, capped(mgrid, static_cast<uint64_t>(L.max_units) * kMerge4Spt), kMerge4Block,
                          smem, keys, vals, kw, vw, recs, list, r, tb));
       }
-    } else if (!(o.debug_flags & 4)) {
+    } else if (o.merge != kMergePerPass) {
       // every merge pass in one persistent launch (dependency-driven queue)
       static PerDevice sgrid_cache;
       int& sgrid = sgrid_cache();
@@ -409,7 +411,7 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
                          tb, sa));
       }
     } else {
-      // per-pass launches (co-rank kernel, then merge kernel), kept as an ablation
+      // per-pass launches: a co-rank kernel, then a merge kernel
       static PerDevice mgrid_cache;
       int& mgrid = mgrid_cache();
       const size_t smem = merge_smem<K, HAS_V, IPT>();

@@ -52,14 +52,15 @@ struct GraphKey {
   uint32_t* vals;
   const uint64_t* offs;
   size_t n, nseg;
-  int partition, stop_after, debug, fan_in, tile;
+  int partition, stop_after, debug, fan_in, tile, merge;
   uint64_t* pkt_out;
   void* ws;
   size_t ws_bytes;
   bool operator<(const GraphKey& o) const {
-    return std::tie(dev, st, dtype, keys, vals, offs, n, nseg, partition, stop_after, debug, fan_in, tile, pkt_out, ws,
+    return std::tie(dev, st, dtype, keys, vals, offs, n, nseg, partition, stop_after, debug, fan_in, tile, merge, pkt_out, ws,
                     ws_bytes) < std::tie(o.dev, o.st, o.dtype, o.keys, o.vals, o.offs, o.n, o.nseg, o.partition,
-                                         o.stop_after, o.debug, o.fan_in, o.tile, o.pkt_out, o.ws, o.ws_bytes);
+                                         o.stop_after, o.debug, o.fan_in, o.tile, o.merge, o.pkt_out, o.ws,
+                                         o.ws_bytes);
   }
 };
 struct GraphEntry {
@@ -132,7 +133,7 @@ struct TuneKey {
 };
 // value: the fan-in and the tile of the shape (0 = the built-in rule's)
 struct TuneVal {
-  int fan_in = 0, tile = 0;
+  int fan_in = 0, tile = 0, merge = 0;
 };
 std::map<TuneKey, TuneVal> g_tune;
 std::mutex g_tune_mu;
@@ -146,7 +147,7 @@ int size_bucket(size_t n) {
 // entry for its (key type, values, partition, size bucket), else the built-in
 // rule from one GB300: four-way passes while passes are short (launch- and
 // latency-bound), two-way passes above 2^21 keys; the default tile.
-void tuned_shape(int dtype, bool has_vals, int partition, size_t n, int* fan_in, int* tile) {
+void tuned_shape(int dtype, bool has_vals, int partition, size_t n, int* fan_in, int* tile, int* merge = nullptr) {
   TuneVal v;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -155,6 +156,12 @@ void tuned_shape(int dtype, bool has_vals, int partition, size_t n, int* fan_in,
   }
   if (fan_in) *fan_in = v.fan_in ? v.fan_in : (n <= (static_cast<size_t>(1) << 21) ? 4 : 2);
   if (tile) *tile = v.tile ? v.tile : sort_tile_for(dtype == HS_UINT64 ? 8 : 4, has_vals);
+  // two-way passes in one persistent launch once passes are long; below, the
+  // queue's pass-to-pass hand-over costs more than a launch per pass
+  // (measured on one GB300: 64-bit keys from 2^25 keys on, 4-byte keys and
+  // pairs above 2^26)
+  const size_t queue_above = static_cast<size_t>(1) << ((dtype == HS_UINT64 && !has_vals) ? 24 : 26);
+  if (merge) *merge = v.merge ? v.merge : (n > queue_above ? kMergeQueue : kMergePerPass);
 }
 int tuned_fan_in(int dtype, bool has_vals, int partition, size_t n) {
   int f = 0;
@@ -201,6 +208,7 @@ hs_status check_opts(const hs_opts* opts, hs_opts* o) {
   if (d.tile != 0 && !tile_built(4, false, d.tile) && !tile_built(4, true, d.tile)) return HS_ERR_UNSUPPORTED;
   if (d.fan_in != 0 && d.fan_in != 2 && d.fan_in != 4) return HS_ERR_UNSUPPORTED;
   if (d.stop_after < 0 || d.stop_after > 2 + kMaxPasses) return HS_ERR_INVALID;
+  if (d.merge != 0 && d.merge != kMergeQueue && d.merge != kMergePerPass) return HS_ERR_UNSUPPORTED;
   *o = d;
   return HS_OK;
 }
@@ -218,10 +226,11 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
     return HS_ERR_INVALID;
   if (o.tile != 0 && !tile_built(key_bytes(dt), vals != nullptr, o.tile)) return HS_ERR_UNSUPPORTED;
   {
-    int f = 0, t = 0;
-    tuned_shape(static_cast<int>(dt), vals != nullptr, o.partition, n, &f, &t);
+    int f = 0, t = 0, m = 0;
+    tuned_shape(static_cast<int>(dt), vals != nullptr, o.partition, n, &f, &t, &m);
     if (o.fan_in == 0) o.fan_in = f;
     if (o.tile == 0) o.tile = t;
+    if (o.merge == 0) o.merge = m;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (n == 0 && !offs) {
@@ -252,7 +261,7 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
   };
   if (!o.graph || st == nullptr || timing_on()) return run();
   const GraphKey key{current_device(), st, static_cast<int>(dt), keys, vals, offs, n, nseg, o.partition,
-                     o.stop_after, o.debug_flags, o.fan_in, o.tile, o.d_packet_offsets_out, ws,
+                     o.stop_after, o.debug_flags, o.fan_in, o.tile, o.merge, o.d_packet_offsets_out, ws,
                      o.d_workspace ? o.workspace_bytes : need};
   auto it = g_graphs.find(key);
   if (it == g_graphs.end()) {
@@ -417,23 +426,28 @@ hs_status hs_tune_set(hs_dtype dtype, int has_vals, int partition, int log2n, in
   return HS_OK;
 }
 
-hs_status hs_tune_set_shape(hs_dtype dtype, int has_vals, int partition, int log2n, int fan_in, int tile) {
+hs_status hs_tune_set_shape(hs_dtype dtype, int has_vals, int partition, int log2n, int fan_in, int tile,
+                            int merge) {
   if (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64) return HS_ERR_INVALID;
   if (partition != 1 && partition != 10 && partition != 256) return HS_ERR_INVALID;
   if (log2n < 0 || log2n > 32 || (fan_in != 0 && fan_in != 2 && fan_in != 4)) return HS_ERR_INVALID;
   if (tile != 0 && !tile_built(key_bytes(dtype), has_vals != 0, tile)) return HS_ERR_INVALID;
+  if (merge != 0 && merge != kMergeQueue && merge != kMergePerPass) return HS_ERR_INVALID;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   TuneVal& v = g_tune[TuneKey{static_cast<int>(dtype), has_vals ? 1 : 0, partition, log2n}];
   v.fan_in = fan_in;
   v.tile = tile;
+  v.merge = merge;
   return HS_OK;
 }
 
-hs_status hs_tune_get_shape(hs_dtype dtype, int has_vals, int partition, size_t n, int* fan_in, int* tile) {
-  if (!fan_in || !tile || (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64)) return HS_ERR_INVALID;
+hs_status hs_tune_get_shape(hs_dtype dtype, int has_vals, int partition, size_t n, int* fan_in, int* tile,
+                            int* merge) {
+  if (!fan_in || !tile || !merge || (dtype != HS_INT32 && dtype != HS_UINT32 && dtype != HS_UINT64))
+    return HS_ERR_INVALID;
   if (partition == 0) partition = 10;
   if (partition != 1 && partition != 10 && partition != 256) return HS_ERR_INVALID;
-  tuned_shape(static_cast<int>(dtype), has_vals != 0, partition, n, fan_in, tile);
+  tuned_shape(static_cast<int>(dtype), has_vals != 0, partition, n, fan_in, tile, merge);
   return HS_OK;
 }
 
@@ -502,10 +516,11 @@ hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, 
   HS_TRY(check_opts(opts, &o));
   if (o.tile != 0 && !tile_built(key_bytes(dtype), has_vals != 0, o.tile)) return HS_ERR_UNSUPPORTED;
   {
-    int f = 0, t = 0;
-    tuned_shape(static_cast<int>(dtype), has_vals != 0, o.partition, n, &f, &t);
+    int f = 0, t = 0, m = 0;
+    tuned_shape(static_cast<int>(dtype), has_vals != 0, o.partition, n, &f, &t, &m);
     if (o.fan_in == 0) o.fan_in = f;
     if (o.tile == 0) o.tile = t;
+    if (o.merge == 0) o.merge = m;
   }
   out->tile = o.tile;
   out->part_tile = kTile;
@@ -525,7 +540,7 @@ hs_status hs_plan_describe(hs_dtype dtype, size_t n, int has_vals, size_t nseg, 
   if (o.stop_after != 1) l += 1;
   // fan-in 2: every merge pass in one persistent launch; fan-in 4 (and the
   // per-pass ablation, debug flag 4): two launches per pass
-  const bool sched = o.fan_in == 2 && !(o.debug_flags & 4);
+  const bool sched = o.fan_in == 2 && o.merge == kMergeQueue;
   auto merge_launches = [&](int p) { return p == 0 ? 0 : (sched ? 1 : 2 * p); };
   if (o.stop_after == 0) l += merge_launches(out->merge_passes);
   if (o.stop_after >= 3) l += merge_launches(std::min(out->merge_passes, o.stop_after - 2)) + 1;

@@ -17,7 +17,8 @@ in a JSON cache:
 
     {"version": 2, "device": "<GPU name>",
      "entries": [{"dtype": "int32", "has_vals": false, "partition": 10, "log2n": 20,
-                  "fan_in": 4, "tile": 3840, "ms": {"2x3840": 0.33, "4x3840": 0.27, ...}}, ...]}
+                  "fan_in": 4, "tile": 3840, "merge": 0,
+                  "ms": {"2x3840q": 0.33, "2x3840p": 0.30, "4x3840": 0.27, ...}}, ...]}
 
 Timing: CUDA events on the sorting stream around one sort, the input restored
 from a pristine copy before every sort (outside the events), the median of
@@ -46,27 +47,36 @@ def size_bucket(n: int) -> int:
     return b
 
 
-def candidates(dtype: int, has_vals: bool = False) -> list[tuple[int, int]]:
-    """Every (fan-in, tile) shape built for this key type."""
+MERGE_QUEUE, MERGE_PER_PASS = 1, 2
+
+
+def candidates(dtype: int, has_vals: bool = False) -> list[tuple[int, int, int]]:
+    """Every (fan-in, tile, merge launch) shape built for this key type (the
+    launch style only matters for two-way passes)."""
     import paper_2003_01216_gb300 as hs
-    return [(f, t) for t in hs.tiles(dtype, has_vals) for f in FANS]
+    out = []
+    for t in hs.tiles(dtype, has_vals):
+        out += [(2, t, MERGE_QUEUE), (2, t, MERGE_PER_PASS), (4, t, 0)]
+    return out
 
 
-def _key(fan: int, tile: int) -> str:
-    return f"{fan}x{tile}"
+def _key(fan: int, tile: int, merge: int = 0) -> str:
+    return f"{fan}x{tile}" + {MERGE_QUEUE: "q", MERGE_PER_PASS: "p"}.get(merge, "")
 
 
-def set_entry(dtype: int, has_vals: bool, partition: int, log2n: int, fan_in: int, tile: int = 0) -> None:
-    N.check(N.lib().hs_tune_set_shape(dtype, int(has_vals), partition, log2n, fan_in, tile), "hs_tune_set_shape")
+def set_entry(dtype: int, has_vals: bool, partition: int, log2n: int, fan_in: int, tile: int = 0,
+              merge: int = 0) -> None:
+    N.check(N.lib().hs_tune_set_shape(dtype, int(has_vals), partition, log2n, fan_in, tile, merge),
+            "hs_tune_set_shape")
 
 
-def get_shape(dtype: int, n: int, has_vals: bool = False, partition: int = 10) -> tuple[int, int]:
-    """The (fan-in, tile) a call with fan_in=0, tile=0 uses for n keys."""
+def get_shape(dtype: int, n: int, has_vals: bool = False, partition: int = 10) -> tuple[int, int, int]:
+    """The (fan-in, tile, merge launch) a call with all three 0 uses for n keys."""
     import ctypes
-    f, t = ctypes.c_int(), ctypes.c_int()
-    N.check(N.lib().hs_tune_get_shape(dtype, int(has_vals), partition, n, ctypes.byref(f), ctypes.byref(t)),
-            "hs_tune_get_shape")
-    return f.value, t.value
+    f, t, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    N.check(N.lib().hs_tune_get_shape(dtype, int(has_vals), partition, n, ctypes.byref(f), ctypes.byref(t),
+                                      ctypes.byref(m)), "hs_tune_get_shape")
+    return f.value, t.value, m.value
 
 
 def get(dtype: int, n: int, has_vals: bool = False, partition: int = 10) -> int:
@@ -79,8 +89,8 @@ def clear() -> None:
 
 
 def measure(dtype: int, n: int, has_vals: bool = False, partition: int = 10, shapes=None,
-            reps: int = 5, warmup: int = 2, seed: int = 0) -> dict[tuple[int, int], float]:
-    """Median milliseconds of one sort of n synthetic keys per (fan-in, tile)."""
+            reps: int = 5, warmup: int = 2, seed: int = 0) -> dict[tuple[int, int, int], float]:
+    """Median milliseconds of one sort of n synthetic keys per shape."""
     import torch
 
     import paper_2003_01216_gb300 as hs
@@ -93,7 +103,7 @@ def measure(dtype: int, n: int, has_vals: bool = False, partition: int = 10, sha
     st = torch.cuda.Stream()
     out = {}
     with torch.cuda.stream(st):
-        for fan, tile in shapes:
+        for fan, tile, merge in shapes:
             ms = []
             for it in range(warmup + reps):
                 work.copy_(pristine)
@@ -102,16 +112,16 @@ def measure(dtype: int, n: int, has_vals: bool = False, partition: int = 10, sha
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(st)
                 if has_vals:
-                    hs.sort_pairs(work, vals, partition=partition, fan_in=fan, tile=tile, stream=st)
+                    hs.sort_pairs(work, vals, partition=partition, fan_in=fan, tile=tile, merge=merge, stream=st)
                 else:
-                    hs.sort_keys(work, partition=partition, fan_in=fan, tile=tile, stream=st)
+                    hs.sort_keys(work, partition=partition, fan_in=fan, tile=tile, merge=merge, stream=st)
                 b.record(st)
                 b.synchronize()
                 if it >= warmup:
                     ms.append(a.elapsed_time(b))
             if hs.stream_error(st) != 0:
-                raise RuntimeError(f"device error while timing fan-in {fan}, tile {tile}")
-            out[(fan, tile)] = statistics.median(ms)
+                raise RuntimeError(f"device error while timing shape {_key(fan, tile, merge)}")
+            out[(fan, tile, merge)] = statistics.median(ms)
     return out
 
 
@@ -121,10 +131,11 @@ def autotune(dtype: int, sizes, has_vals: bool = False, partition: int = 10, rep
     entries = []
     for n in sizes:
         ms = measure(dtype, n, has_vals, partition, reps=reps)
-        fan, tile = min(ms, key=ms.get)
+        fan, tile, merge = min(ms, key=ms.get)
         e = {"dtype": DTYPE_NAMES[dtype], "has_vals": bool(has_vals), "partition": partition,
-             "log2n": size_bucket(n), "fan_in": fan, "tile": tile, "ms": {_key(*k): v for k, v in ms.items()}}
-        set_entry(dtype, has_vals, partition, e["log2n"], fan, tile)
+             "log2n": size_bucket(n), "fan_in": fan, "tile": tile, "merge": merge,
+             "ms": {_key(*k): v for k, v in ms.items()}}
+        set_entry(dtype, has_vals, partition, e["log2n"], fan, tile, merge)
         entries.append(e)
     return entries
 
@@ -158,6 +169,6 @@ def load(path: str, device: str | None = None, any_device: bool = False) -> int:
     k = 0
     for e in doc["entries"]:
         set_entry(DTYPE_CODES[e["dtype"]], bool(e["has_vals"]), int(e["partition"]), int(e["log2n"]), int(e["fan_in"]),
-                  int(e.get("tile", 0)))
+                  int(e.get("tile", 0)), int(e.get("merge", 0)))
         k += 1
     return k

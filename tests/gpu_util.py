@@ -18,7 +18,7 @@ def to_dev(a: np.ndarray):
 
 
 def run(keys: np.ndarray, vals: np.ndarray | None = None, nb: int = 10, stop_after: int = 0, debug_flags: int = 0,
-        fan_in: int = 0, tile: int = 0):
+        fan_in: int = 0, tile: int = 0, merge: int = 0):
     """One hs_sort_keys / hs_sort_pairs call; returns (keys, vals, offsets, status)."""
     import torch
 
@@ -28,10 +28,10 @@ def run(keys: np.ndarray, vals: np.ndarray | None = None, nb: int = 10, stop_aft
     off = torch.zeros(nb + 1, dtype=torch.uint64, device=dev())
     if tv is None:
         hs.sort_keys(tk, partition=nb, stop_after=stop_after, packet_offsets=off, debug_flags=debug_flags,
-                     fan_in=fan_in, tile=tile)
+                     fan_in=fan_in, tile=tile, merge=merge)
     else:
         hs.sort_pairs(tk, tv, partition=nb, stop_after=stop_after, packet_offsets=off, debug_flags=debug_flags,
-                      fan_in=fan_in, tile=tile)
+                      fan_in=fan_in, tile=tile, merge=merge)
     st = hs.stream_error()
     return tk.cpu().numpy(), (tv.cpu().numpy() if tv is not None else None), off.cpu().numpy(), st
 

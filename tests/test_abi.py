@@ -93,15 +93,19 @@ def test_plan_describe(n):
         # an array of at most one tile is sorted whole by the tile sort launch:
         # seg_plan, the one-CTA plan, tile sort
         short = n <= tile
-        # fan-in 2: every merge pass in one persistent launch (the per-pass
-        # ablation, debug flag 4, takes a co-rank and a merge launch per pass)
+        # fan-in 2: every merge pass in one persistent launch (merge = 1), or a
+        # co-rank and a merge launch per pass (merge = 2); the default takes
+        # the queue above 2^24 keys
         sched = 1 if passes else 0
-        assert p["launches"] == (3 if short else 1 + hist + (1 if small else 7) + 2 + sched)
-        per_pass = hs.plan(dtype, n, has_vals, fan_in=2, debug_flags=4)["launches"]
+        q = hs.plan(dtype, n, has_vals, fan_in=2, merge=1)
+        assert q["launches"] == (3 if short else 1 + hist + (1 if small else 7) + 2 + sched)
+        per_pass = hs.plan(dtype, n, has_vals, fan_in=2, merge=2)["launches"]
         assert per_pass == (3 if short else 1 + hist + (1 if small else 7) + 2 + 2 * passes)
+        queue_above = 1 << (24 if (dtype == N.HS_UINT64 and not has_vals) else 26)
+        assert p["launches"] == (q["launches"] if n > queue_above else per_pass)
         # without the MSD step: seg_plan, packet table, tile prefix, tile sort
         small1 = blocks <= 1 << 16
-        assert hs.plan(dtype, n, has_vals, partition=1, fan_in=2)["launches"] == (
+        assert hs.plan(dtype, n, has_vals, partition=1, fan_in=2, merge=1)["launches"] == (
             3 if short else (3 if small1 else 4) + sched)
         # the testing stop after the tile sort keeps the packet step
         assert hs.plan(dtype, n, has_vals, fan_in=2, stop_after=2)["launches"] == (
@@ -118,11 +122,11 @@ def test_stop_after_merge_pass_plan():
     import paper_2003_01216_gb300 as hs
     full = hs.plan(N.HS_INT32, 1 << 24, fan_in=2)
     for r in (1, 3, full["merge_passes"], full["merge_passes"] + 5):
-        p = hs.plan(N.HS_INT32, 1 << 24, fan_in=2, stop_after=2 + r)
+        p = hs.plan(N.HS_INT32, 1 << 24, fan_in=2, stop_after=2 + r, merge=1)
         # the passes up to r (one scheduler launch), then one copy-back kernel
-        assert p["launches"] == full["launches"] + 1
-        q = hs.plan(N.HS_INT32, 1 << 24, fan_in=2, stop_after=2 + r, debug_flags=4)
-        assert q["launches"] == full["launches"] - 1 + 2 * min(r, full["merge_passes"]) + 1
+        assert p["launches"] == hs.plan(N.HS_INT32, 1 << 24, fan_in=2, merge=1)["launches"] + 1
+        q = hs.plan(N.HS_INT32, 1 << 24, fan_in=2, stop_after=2 + r, merge=2)
+        assert q["launches"] == full["launches"] - 2 * full["merge_passes"] + 2 * min(r, full["merge_passes"]) + 1
     lib = N.lib()
     assert lib.hs_sort_keys(0, ctypes.c_void_p(0x1000), 10, ctypes.byref(N.make_opts(stop_after=67)), None) == \
         N.HS_ERR_INVALID
@@ -201,22 +205,28 @@ def test_tile_shapes_and_tuning_table():
     with pytest.raises(hs.HsError):
         hs.plan(N.HS_UINT64, 1 << 20, tile=7936)
     lib = N.lib()
-    fan, tile = ctypes.c_int(), ctypes.c_int()
+    fan, tile, merge = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    shape = (ctypes.byref(fan), ctypes.byref(tile), ctypes.byref(merge))
     lib.hs_tune_clear()
     try:
-        assert lib.hs_tune_get_shape(0, 0, 10, 1 << 20, ctypes.byref(fan), ctypes.byref(tile)) == N.HS_OK
-        assert (fan.value, tile.value) == (4, 7936)  # the built-in rule
-        assert lib.hs_tune_set_shape(0, 0, 10, 20, 2, 3840) == N.HS_OK
-        assert lib.hs_tune_get_shape(0, 0, 10, 1 << 20, ctypes.byref(fan), ctypes.byref(tile)) == N.HS_OK
-        assert (fan.value, tile.value) == (2, 3840)
+        assert lib.hs_tune_get_shape(0, 0, 10, 1 << 20, *shape) == N.HS_OK
+        assert (fan.value, tile.value, merge.value) == (4, 7936, 2)  # the built-in rule
+        assert lib.hs_tune_get_shape(0, 0, 10, 1 << 28, *shape) == N.HS_OK
+        assert (fan.value, tile.value, merge.value) == (2, 7936, 1)
+        assert lib.hs_tune_set_shape(0, 0, 10, 20, 2, 3840, 1) == N.HS_OK
+        assert lib.hs_tune_get_shape(0, 0, 10, 1 << 20, *shape) == N.HS_OK
+        assert (fan.value, tile.value, merge.value) == (2, 3840, 1)
         assert hs.plan(N.HS_INT32, 1 << 20)["tile"] == 3840  # tile = 0 takes the table's
         assert hs.plan(N.HS_INT32, 1 << 21)["tile"] == 7936  # another size bucket
         # the fan-in alone keeps the tuned tile
         assert lib.hs_tune_set(0, 0, 10, 20, 4) == N.HS_OK
-        assert lib.hs_tune_get_shape(0, 0, 10, 1 << 20, ctypes.byref(fan), ctypes.byref(tile)) == N.HS_OK
-        assert (fan.value, tile.value) == (4, 3840)
+        assert lib.hs_tune_get_shape(0, 0, 10, 1 << 20, *shape) == N.HS_OK
+        assert (fan.value, tile.value, merge.value) == (4, 3840, 1)
         # shapes not built for the key type are refused
-        assert lib.hs_tune_set_shape(2, 0, 10, 20, 2, 7936) == N.HS_ERR_INVALID
-        assert lib.hs_tune_set_shape(0, 0, 10, 20, 3, 3840) == N.HS_ERR_INVALID
+        assert lib.hs_tune_set_shape(2, 0, 10, 20, 2, 7936, 0) == N.HS_ERR_INVALID
+        assert lib.hs_tune_set_shape(0, 0, 10, 20, 3, 3840, 0) == N.HS_ERR_INVALID
+        assert lib.hs_tune_set_shape(0, 0, 10, 20, 2, 3840, 3) == N.HS_ERR_INVALID
+        with pytest.raises(hs.HsError):
+            hs.plan(N.HS_INT32, 1 << 20, merge=5)
     finally:
         lib.hs_tune_clear()

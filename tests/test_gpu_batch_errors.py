@@ -12,6 +12,11 @@ from paper_2003_01216_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
+# merge shapes: two-way passes in one persistent launch (merge = 1), two-way
+# passes with a launch each (merge = 2), four-way passes
+SHAPES = [(2, 1), (2, 2), (4, 0)]
+SHAPE_IDS = ["fan2-queue", "fan2-per-pass", "fan4"]
+
 
 def make_batch(count, lo, hi, seed, empties=True):
     lens = I.log_uniform_lengths(count, lo, hi, seed=seed)
@@ -22,10 +27,10 @@ def make_batch(count, lo, hi, seed, empties=True):
     return off
 
 
-@pytest.mark.parametrize("fan", [2, 4])
+@pytest.mark.parametrize("fan,merge", SHAPES, ids=SHAPE_IDS)
 @pytest.mark.parametrize("nb", [1, 10, 256])
 @pytest.mark.parametrize("dist", ["uniform31", "zipf", "int32full", "uniform32", "uniform64", "distinct2p24"])
-def test_sort_batch(oracle, dist, nb, fan):
+def test_sort_batch(oracle, dist, nb, fan, merge):
     off = make_batch(300, 1, 20_000, seed=5)
     n = int(off[-1])
     keys = I.generate(dist, n, seed=6)
@@ -33,12 +38,12 @@ def test_sort_batch(oracle, dist, nb, fan):
     ek, ev = oracle.sort_batch(keys, off, vals, nbuckets=nb)
     tk, tv, to = to_dev(keys), to_dev(vals), to_dev(off)
     poff = torch.zeros(300 * nb + 1, dtype=torch.uint64, device=dev())
-    hs.sort_batch(tk, to, tv, partition=nb, packet_offsets=poff, fan_in=fan)
+    hs.sort_batch(tk, to, tv, partition=nb, packet_offsets=poff, fan_in=fan, merge=merge)
     assert hs.stream_error() == 0
     assert_equal(tk.cpu().numpy(), ek, f"batch keys {dist}")
     assert_equal(tv.cpu().numpy(), ev, f"batch values {dist}")
     tk = to_dev(keys)
-    hs.sort_batch(tk, to, None, partition=nb, fan_in=fan)
+    hs.sort_batch(tk, to, None, partition=nb, fan_in=fan, merge=merge)
     assert hs.stream_error() == 0
     assert_equal(tk.cpu().numpy(), ek, f"batch keys only {dist}")
     # packet offsets of every segment equal the oracle's, shifted by the segment start
@@ -121,9 +126,9 @@ def test_streams_do_not_share_work_space(oracle):
     assert_equal(tb.cpu().numpy(), oracle.sort(b)[0], "stream 2")
 
 
-@pytest.mark.parametrize("fan", [2, 4])
+@pytest.mark.parametrize("fan,merge", SHAPES, ids=SHAPE_IDS)
 @pytest.mark.parametrize("nb", [10, 256])
-def test_batch_graph_replay(oracle, nb, fan):
+def test_batch_graph_replay(oracle, nb, fan, merge):
     # the whole call captured once in a CUDA graph, then replayed on new data
     off = make_batch(500, 1, 30_000, seed=15)
     n = int(off[-1])
@@ -135,7 +140,7 @@ def test_batch_graph_replay(oracle, nb, fan):
         ek, _ = oracle.sort_batch(keys, off, nbuckets=nb)
         with torch.cuda.stream(st):
             work.copy_(torch.from_numpy(keys))
-            hs.sort_batch(work, to, partition=nb, graph=True, fan_in=fan)
+            hs.sort_batch(work, to, partition=nb, graph=True, fan_in=fan, merge=merge)
         assert hs.stream_error(st) == 0
         assert_equal(work.cpu().numpy(), ek, f"graph replay seed {seed}")
     hs.graph_cache_clear()
@@ -165,22 +170,24 @@ def test_autotune_installs_a_correct_choice(oracle):
     try:
         entries = tune.autotune(0, [1 << 16, 3 << 18], reps=2)
         assert [e["log2n"] for e in entries] == [16, 20]
-        shapes = [(f, t) for t in hs.tiles(0) for f in (2, 4)]
+        shapes = tune.candidates(0)
+        assert len(shapes) == 3 * len(hs.tiles(0))
         for e in entries:
-            assert set(e["ms"]) == {f"{f}x{t}" for f, t in shapes}
-            best = min(shapes, key=lambda ft: e["ms"][f"{ft[0]}x{ft[1]}"])
-            assert (e["fan_in"], e["tile"]) == best
-            assert tune.get_shape(0, 1 << e["log2n"]) == best
+            assert set(e["ms"]) == {tune._key(*sh) for sh in shapes}
+            best = min(shapes, key=lambda sh: e["ms"][tune._key(*sh)])
+            assert (e["fan_in"], e["tile"], e["merge"]) == best
+            f, t, m = tune.get_shape(0, 1 << e["log2n"])
+            assert (f, t) == best[:2] and (m == best[2] or best[0] == 4)
             assert hs.plan(0, 1 << e["log2n"])["tile"] == e["tile"]
         keys = I.generate("zipf", 3 << 18, seed=44)
         gk, _, _, st = run(keys)  # fan_in = 0, tile = 0: the tuned entry
         assert st == 0
         assert_equal(gk, oracle.sort(keys)[0], "sort with the tuned shape")
         # every tile the tuner may install sorts correctly at this size
-        for f, t in shapes:
-            gk, _, _, st = run(keys, fan_in=f, tile=t)
+        for f, t, m in shapes:
+            gk, _, _, st = run(keys, fan_in=f, tile=t, merge=m)
             assert st == 0
-            assert_equal(gk, oracle.sort(keys)[0], f"sort with fan-in {f}, tile {t}")
+            assert_equal(gk, oracle.sort(keys)[0], f"sort with shape {tune._key(f, t, m)}")
     finally:
         tune.clear()
 
@@ -192,10 +199,10 @@ def test_merge_queue_wait_expires_and_context_survives(oracle):
     # reports HS_ERR_TIMEOUT
     keys = I.generate("uniform31", 100_000, seed=15)  # two packets of ~6 tiles: three passes
     assert hs.plan(0, keys.size, fan_in=2)["merge_passes"] >= 2
-    _, _, _, st = run(keys, debug_flags=2, fan_in=2)
+    _, _, _, st = run(keys, debug_flags=2, fan_in=2, merge=1)
     assert st == HS_TIMEOUT
     # the context stays usable and the next call is correct
-    gk, _, _, st = run(keys, fan_in=2)
+    gk, _, _, st = run(keys, fan_in=2, merge=1)
     assert st == 0
     assert_equal(gk, oracle.sort(keys)[0], "sort after an expired merge-queue wait")
 
@@ -203,13 +210,12 @@ def test_merge_queue_wait_expires_and_context_survives(oracle):
 @pytest.mark.parametrize("dist,n,with_vals", [("uniform31", 3_000_000, False), ("zipf", 1_500_000, True),
                                               ("uniform64", 1_000_000, True), ("sorted", 2_000_000, False)])
 def test_merge_queue_equals_per_pass_launches(oracle, dist, n, with_vals):
-    # one persistent merge launch (default for fan-in 2) against one co-rank
-    # and one merge launch per pass (debug flag 4): the same bits, and the
-    # oracle's
+    # one persistent merge launch (merge = 1) against one co-rank and one
+    # merge launch per pass (merge = 2): the same bits, and the oracle's
     keys = I.generate(dist, n, seed=16)
     vals = I.index_values(n) if with_vals else None
-    a = run(keys, vals, fan_in=2)
-    b = run(keys, vals, fan_in=2, debug_flags=4)
+    a = run(keys, vals, fan_in=2, merge=1)
+    b = run(keys, vals, fan_in=2, merge=2)
     assert a[3] == 0 and b[3] == 0
     assert_equal(a[0], b[0], "keys: queue vs per-pass")
     ek, ev, eo = oracle.sort(keys, vals)

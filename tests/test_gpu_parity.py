@@ -12,6 +12,11 @@ from paper_2003_01216_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
+# merge shapes: two-way passes in one persistent launch (merge = 1), two-way
+# passes with a launch each (merge = 2), four-way passes
+SHAPES = [(2, 1), (2, 2), (4, 0)]
+SHAPE_IDS = ["fan2-queue", "fan2-per-pass", "fan4"]
+
 TILE = hs.plan(0, 1 << 20)["tile"]                    # int32 keys: keys per tile and merge block
 TILE_PAIRS = hs.plan(0, 1 << 20, has_vals=True)["tile"]  # pairs (and 64-bit keys)
 PART = hs.plan(0, 1 << 20)["part_tile"]                # keys per packet-step block
@@ -70,29 +75,29 @@ def test_tilesort_stage(oracle, dist, nb):
         assert_equal(gk, ek, f"tile-sorted keys (keys only) {dist} n={n}")
 
 
-@pytest.mark.parametrize("fan", [2, 4])
+@pytest.mark.parametrize("fan,merge", SHAPES, ids=SHAPE_IDS)
 @pytest.mark.parametrize("nb", [1, 10, 256])
 @pytest.mark.parametrize("dist", DISTS)
-def test_sort_keys(oracle, dist, nb, fan):
+def test_sort_keys(oracle, dist, nb, fan, merge):
     for n in SIZES:
         keys = I.generate(dist, n, seed=3)
         ek, _, eoff = oracle.sort(keys, None, nb)
-        gk, _, goff, st = run(keys, None, nb, fan_in=fan)
+        gk, _, goff, st = run(keys, None, nb, fan_in=fan, merge=merge)
         assert st == 0
         assert_equal(gk, ek, f"sorted keys {dist} n={n}")
         assert_equal(goff, eoff, f"packet offsets {dist} n={n}")
 
 
-@pytest.mark.parametrize("fan", [2, 4])
+@pytest.mark.parametrize("fan,merge", SHAPES, ids=SHAPE_IDS)
 @pytest.mark.parametrize("nb", [1, 10, 256])
 @pytest.mark.parametrize("dist", ["uniform31", "zipf", "equal", "distinct16", "int32full", "uniform32",
                                   "uniform64", "distinct2p24"])
-def test_sort_pairs_stable(oracle, dist, nb, fan):
+def test_sort_pairs_stable(oracle, dist, nb, fan, merge):
     for n in SIZES:
         keys = I.generate(dist, n, seed=4)
         vals = I.index_values(n)
         ek, ev, _ = oracle.sort(keys, vals, nb)
-        gk, gv, _, st = run(keys, vals, nb, fan_in=fan)
+        gk, gv, _, st = run(keys, vals, nb, fan_in=fan, merge=merge)
         assert st == 0
         assert_equal(gk, ek, f"pair keys {dist} n={n}")
         assert_equal(gv, ev, f"pair values (stable order) {dist} n={n}")
@@ -179,20 +184,20 @@ def test_persistent_ctas_loop_over_many_blocks(oracle, dist):
         assert_equal(gk, lk, f"{dist} packet layout (pass {rep})")
         assert_equal(gv, lv, f"{dist} packet layout values (pass {rep})")
     ek, ev, _ = oracle.sort(keys, vals, 10)
-    for fan in (2, 4):
-        gk, gv, _, st = run(keys, vals, 10, fan_in=fan)
+    for fan, merge in SHAPES:
+        gk, gv, _, st = run(keys, vals, 10, fan_in=fan, merge=merge)
         assert st == 0
         assert_equal(gk, ek, f"{dist} pair keys fan-in {fan}")
         assert_equal(gv, ev, f"{dist} pair values fan-in {fan}")
-        gk, _, _, st = run(keys, None, 10, fan_in=fan)
+        gk, _, _, st = run(keys, None, 10, fan_in=fan, merge=merge)
         assert st == 0
         assert_equal(gk, ek, f"{dist} keys fan-in {fan}")
 
 
-@pytest.mark.parametrize("fan", [2, 4])
+@pytest.mark.parametrize("fan,merge", SHAPES, ids=SHAPE_IDS)
 @pytest.mark.parametrize("nb", [1, 10])
 @pytest.mark.parametrize("dist", ["uniform1e9", "zipf", "uniform64", "distinct2p24"])
-def test_merge_passes_one_by_one(oracle, dist, nb, fan):
+def test_merge_passes_one_by_one(oracle, dist, nb, fan, merge):
     # the state after every merge pass r: inside each packet every group of
     # fan^r tiles is sorted on its own (pairs stably), the rest untouched by
     # later passes -- the oracle's tile sort with tile * fan^r
@@ -207,7 +212,7 @@ def test_merge_passes_one_by_one(oracle, dist, nb, fan):
         assert passes >= 2
         for r in range(1, passes + 1):
             ek, ev = oracle.tile_sort(lk, off, tile * fan ** r, lv if has_vals else None)
-            gk, gv, goff, st = run(keys, vals if has_vals else None, nb, stop_after=2 + r, fan_in=fan)
+            gk, gv, goff, st = run(keys, vals if has_vals else None, nb, stop_after=2 + r, fan_in=fan, merge=merge)
             assert st == 0
             assert_equal(goff, off, f"{dist} packet offsets after pass {r}")
             assert_equal(gk, ek, f"{dist} keys after merge pass {r} (fan-in {fan}, values {has_vals})")
