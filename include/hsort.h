@@ -108,8 +108,8 @@ typedef struct {
                            (packet, pass, merge block) items each started as soon as the runs
                            it reads are complete; 2 = one co-rank and one merge launch per
                            pass; 0 = tuned: the tuning table's entry, else 1 above 2^24 keys
-                           (64-bit keys without values) or 2^26 keys (otherwise) and 2 up to
-                           it.  Other values: HS_ERR_UNSUPPORTED */
+                           (64-bit keys without values) or 2^26 keys (4-byte keys without
+                           values), 2 otherwise.  Other values: HS_ERR_UNSUPPORTED */
 } hs_opts;
 
 /*

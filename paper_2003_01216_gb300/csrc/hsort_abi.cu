@@ -158,10 +158,10 @@ void tuned_shape(int dtype, bool has_vals, int partition, size_t n, int* fan_in,
   if (tile) *tile = v.tile ? v.tile : sort_tile_for(dtype == HS_UINT64 ? 8 : 4, has_vals);
   // two-way passes in one persistent launch once passes are long; below, the
   // queue's pass-to-pass hand-over costs more than a launch per pass
-  // (measured on one GB300: 64-bit keys from 2^25 keys on, 4-byte keys and
-  // pairs above 2^26)
-  const size_t queue_above = static_cast<size_t>(1) << ((dtype == HS_UINT64 && !has_vals) ? 24 : 26);
-  if (merge) *merge = v.merge ? v.merge : (n > queue_above ? kMergeQueue : kMergePerPass);
+  // (measured on one GB300: 64-bit keys from 2^25 keys on, 4-byte keys above
+  // 2^26; key-value pairs up to 2^27, the largest size measured, never)
+  const bool queue = !has_vals && n > (static_cast<size_t>(1) << (dtype == HS_UINT64 ? 24 : 26));
+  if (merge) *merge = v.merge ? v.merge : (queue ? kMergeQueue : kMergePerPass);
 }
 int tuned_fan_in(int dtype, bool has_vals, int partition, size_t n) {
   int f = 0;

@@ -101,8 +101,8 @@ def test_plan_describe(n):
         assert q["launches"] == (3 if short else 1 + hist + (1 if small else 7) + 2 + sched)
         per_pass = hs.plan(dtype, n, has_vals, fan_in=2, merge=2)["launches"]
         assert per_pass == (3 if short else 1 + hist + (1 if small else 7) + 2 + 2 * passes)
-        queue_above = 1 << (24 if (dtype == N.HS_UINT64 and not has_vals) else 26)
-        assert p["launches"] == (q["launches"] if n > queue_above else per_pass)
+        queue = not has_vals and n > 1 << (24 if dtype == N.HS_UINT64 else 26)
+        assert p["launches"] == (q["launches"] if queue else per_pass)
         # without the MSD step: seg_plan, packet table, tile prefix, tile sort
         small1 = blocks <= 1 << 16
         assert hs.plan(dtype, n, has_vals, partition=1, fan_in=2, merge=1)["launches"] == (
