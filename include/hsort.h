@@ -151,10 +151,17 @@ hs_status hs_sort_batch(hs_dtype dtype, void* d_keys, uint32_t* d_vals, const ui
                         size_t nseg, size_t n, const hs_opts* opts, void* stream);
 
 /*
- * hs_sort_keys_host -- the same sort for keys in HOST memory: copies the n
- * keys to the device (library-owned staging buffer), sorts them, copies them
- * back and synchronises `stream` before returning.  Pinned host memory gives
- * the fastest copies; pageable memory works.
+ * hs_sort_keys_host -- the same sort for keys in HOST memory: the n keys go
+ * to a library-owned device staging buffer, are sorted there and are copied
+ * back; `stream` is synchronised before returning.  Pinned host memory that
+ * the device can address (cudaHostAlloc / cudaMallocHost, or registered with
+ * cudaHostRegister and mapped; with unified addressing every pinned block is)
+ * is read by the sort's first pass itself: the histogram kernel loads the
+ * keys from host memory and writes them to the staging buffer while it
+ * counts them, so the copy in and the histogram are one pass (a call without
+ * a histogram -- partition 1, or n of at most one tile -- copies them in
+ * first).  Pageable memory is copied in with cudaMemcpyAsync.  Same result
+ * either way.
  */
 hs_status hs_sort_keys_host(hs_dtype dtype, void* h_keys, size_t n, const hs_opts* opts, void* stream);
 

@@ -250,10 +250,13 @@ hs_status launch_bound4(Launcher& lc, K* keys, K* kw, Rec4* recs, uint32_t* list
 
 // One sort call.  keys/vals: the caller's arrays (U).  offs: batch offsets
 // (device) or nullptr for one segment.  ws: work space of at least
-// make_layout(...).total bytes.
+// make_layout(...).total bytes.  src: nullptr, or the keys in pinned host
+// memory the device can address (one segment, no values): the histogram
+// reads them from there and writes them into `keys` in the same pass (a
+// call without a histogram copies them in first).
 template <class K, bool HAS_V, int NB, int IPT>
 hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
-                      char* ws, uint32_t* err, cudaStream_t st) {
+                      char* ws, uint32_t* err, cudaStream_t st, const K* src) {
   const Layout L = make_layout(sizeof(K), n, HAS_V, nseg, NB);
   const int fan = o.fan_in == 4 ? 4 : 2;
   Tables tb = make_tables(ws, L, err, fan_log2_of(fan));
@@ -278,6 +281,9 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
   // one segment known on the host to be short: no packet-step kernels at all
   const bool all_short = nseg == 1 && n <= small_max;
   HS_TRY(lc.kernel("seg_plan", k_seg_plan, 1, 1024, 0, offs, nseg32, n, kTile, small_max, tb));
+  // keys in host memory and no histogram to read them: copy them in
+  const bool hist_reads_src = src != nullptr && NB != 1 && !all_short;
+  if (src && !hist_reads_src) HS_TRY(lc.copy("copy_in", keys, src, n * sizeof(K), cudaMemcpyHostToDevice));
 
   if constexpr (NB == 1) {
     // no MSD step (ablation): every segment is one packet; the tile sort
@@ -290,14 +296,21 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
     }
   } else {
     if (!all_short) {
-      static PerDevice grid_cache;
+      static PerDevice grid_cache, sgrid_cache;
       int& grid = grid_cache();
+      int& sgrid = sgrid_cache();
       const size_t smem = hist_smem<K>();
       auto kern = k_hist<K, NB, kBlock, kIpt>;
+      auto skern = k_hist<K, NB, kBlock, kIpt, true>;  // reads the keys from host memory
       if (!grid) grid = persistent_grid(kern, kBlock, smem);
+      if (hist_reads_src && !sgrid) sgrid = persistent_grid(skern, kBlock, 0);
       for (int img = 0; img < (std::is_same<K, int32_t>::value ? 2 : 1); ++img) {
-        HS_TRY(lc.kernel(img ? "hist_flip" : "hist", kern, capped(grid, L.max_blocks), kBlock, smem, keys, nseg32, kTile,
-                         img, tb));
+        if (img == 0 && hist_reads_src)
+          HS_TRY(lc.kernel("hist_copy_in", skern, capped(sgrid, L.max_blocks), kBlock, 0, keys, src, nseg32, kTile,
+                           img, tb));
+        else
+          HS_TRY(lc.kernel(img ? "hist_flip" : "hist", kern, capped(grid, L.max_blocks), kBlock, smem, keys,
+                           static_cast<const K*>(nullptr), nseg32, kTile, img, tb));
       }
     }
     if (small) {
@@ -444,21 +457,24 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
 // translation unit per (key type, IPT) (sort_shape.cu).
 template <class K, bool HAS_V, int IPT>
 hs_status run_sort_part(K* k, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
-                        char* ws, uint32_t* err, cudaStream_t st) {
-  if (o.partition == 1) return run_sort_nb<K, HAS_V, 1, IPT>(k, vals, n, nseg, offs, o, ws, err, st);
-  if (o.partition == 256) return run_sort_nb<K, HAS_V, 256, IPT>(k, vals, n, nseg, offs, o, ws, err, st);
-  return run_sort_nb<K, HAS_V, 10, IPT>(k, vals, n, nseg, offs, o, ws, err, st);
+                        char* ws, uint32_t* err, cudaStream_t st, const K* src) {
+  if (o.partition == 1) return run_sort_nb<K, HAS_V, 1, IPT>(k, vals, n, nseg, offs, o, ws, err, st, src);
+  if (o.partition == 256) return run_sort_nb<K, HAS_V, 256, IPT>(k, vals, n, nseg, offs, o, ws, err, st, src);
+  return run_sort_nb<K, HAS_V, 10, IPT>(k, vals, n, nseg, offs, o, ws, err, st, src);
 }
 
 template <class K, int IPT>
 hs_status run_sort_ipt(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
-                       char* ws, uint32_t* err, cudaStream_t st) {
+                       char* ws, uint32_t* err, cudaStream_t st, const void* src) {
   K* k = static_cast<K*>(keys);
+  const K* ks = static_cast<const K*>(src);
+  if (src && (vals || nseg != 1)) return HS_ERR_INVALID;  // host keys: one array, keys only
   if (vals) {
-    if constexpr (ipt_built<K, true, IPT>()) return run_sort_part<K, true, IPT>(k, vals, n, nseg, offs, o, ws, err, st);
+    if constexpr (ipt_built<K, true, IPT>())
+      return run_sort_part<K, true, IPT>(k, vals, n, nseg, offs, o, ws, err, st, nullptr);
     else return HS_ERR_UNSUPPORTED;
   } else {
-    if constexpr (ipt_built<K, false, IPT>()) return run_sort_part<K, false, IPT>(k, vals, n, nseg, offs, o, ws, err, st);
+    if constexpr (ipt_built<K, false, IPT>()) return run_sort_part<K, false, IPT>(k, vals, n, nseg, offs, o, ws, err, st, ks);
     else return HS_ERR_UNSUPPORTED;
   }
 }

@@ -56,11 +56,12 @@ struct GraphKey {
   uint64_t* pkt_out;
   void* ws;
   size_t ws_bytes;
+  const void* src;
   bool operator<(const GraphKey& o) const {
     return std::tie(dev, st, dtype, keys, vals, offs, n, nseg, partition, stop_after, debug, fan_in, tile, merge, pkt_out, ws,
-                    ws_bytes) < std::tie(o.dev, o.st, o.dtype, o.keys, o.vals, o.offs, o.n, o.nseg, o.partition,
-                                         o.stop_after, o.debug, o.fan_in, o.tile, o.merge, o.pkt_out, o.ws,
-                                         o.ws_bytes);
+                    ws_bytes, src) < std::tie(o.dev, o.st, o.dtype, o.keys, o.vals, o.offs, o.n, o.nseg, o.partition,
+                                              o.stop_after, o.debug, o.fan_in, o.tile, o.merge, o.pkt_out, o.ws,
+                                              o.ws_bytes, o.src);
   }
 };
 struct GraphEntry {
@@ -171,29 +172,29 @@ int tuned_fan_in(int dtype, bool has_vals, int partition, size_t n) {
 
 // The per-(key type, tile shape) entry points of sort_shape.cu.
 hs_status run_shape(hs_dtype dt, int tile, void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs,
-                    const hs_opts& o, char* ws, uint32_t* err, cudaStream_t st) {
+                    const hs_opts& o, char* ws, uint32_t* err, cudaStream_t st, const void* src) {
   const int ipt = tile / kBlock;
   switch (dt) {
     case HS_INT32:
       switch (ipt) {
-        case 11: return run_sort_i32_t11(keys, vals, n, nseg, offs, o, ws, err, st);
-        case 15: return run_sort_i32_t15(keys, vals, n, nseg, offs, o, ws, err, st);
-        case 23: return run_sort_i32_t23(keys, vals, n, nseg, offs, o, ws, err, st);
-        case 31: return run_sort_i32_t31(keys, vals, n, nseg, offs, o, ws, err, st);
+        case 11: return run_sort_i32_t11(keys, vals, n, nseg, offs, o, ws, err, st, src);
+        case 15: return run_sort_i32_t15(keys, vals, n, nseg, offs, o, ws, err, st, src);
+        case 23: return run_sort_i32_t23(keys, vals, n, nseg, offs, o, ws, err, st, src);
+        case 31: return run_sort_i32_t31(keys, vals, n, nseg, offs, o, ws, err, st, src);
       }
       break;
     case HS_UINT32:
       switch (ipt) {
-        case 11: return run_sort_u32_t11(keys, vals, n, nseg, offs, o, ws, err, st);
-        case 15: return run_sort_u32_t15(keys, vals, n, nseg, offs, o, ws, err, st);
-        case 23: return run_sort_u32_t23(keys, vals, n, nseg, offs, o, ws, err, st);
-        case 31: return run_sort_u32_t31(keys, vals, n, nseg, offs, o, ws, err, st);
+        case 11: return run_sort_u32_t11(keys, vals, n, nseg, offs, o, ws, err, st, src);
+        case 15: return run_sort_u32_t15(keys, vals, n, nseg, offs, o, ws, err, st, src);
+        case 23: return run_sort_u32_t23(keys, vals, n, nseg, offs, o, ws, err, st, src);
+        case 31: return run_sort_u32_t31(keys, vals, n, nseg, offs, o, ws, err, st, src);
       }
       break;
     default:
       switch (ipt) {
-        case 11: return run_sort_u64_t11(keys, vals, n, nseg, offs, o, ws, err, st);
-        case 15: return run_sort_u64_t15(keys, vals, n, nseg, offs, o, ws, err, st);
+        case 11: return run_sort_u64_t11(keys, vals, n, nseg, offs, o, ws, err, st, src);
+        case 15: return run_sort_u64_t15(keys, vals, n, nseg, offs, o, ws, err, st, src);
       }
       break;
   }
@@ -213,8 +214,10 @@ hs_status check_opts(const hs_opts* opts, hs_opts* o) {
   return HS_OK;
 }
 
+// src: nullptr, or the keys in pinned host memory the device can address
+// (hs_sort_keys_host); `keys` is then the device array they are sorted in.
 hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs,
-                   const hs_opts* opts, void* stream) {
+                   const hs_opts* opts, void* stream, const void* src = nullptr) {
   if (dt != HS_INT32 && dt != HS_UINT32 && dt != HS_UINT64) return HS_ERR_INVALID;
   hs_opts o;
   HS_TRY(check_opts(opts, &o));
@@ -256,13 +259,13 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
   }
   auto run = [&]() -> hs_status {
     switch (dt) {
-      default: return run_shape(dt, o.tile, keys, vals, n, nseg, offs, o, ws, err, st);
+      default: return run_shape(dt, o.tile, keys, vals, n, nseg, offs, o, ws, err, st, src);
     }
   };
   if (!o.graph || st == nullptr || timing_on()) return run();
   const GraphKey key{current_device(), st, static_cast<int>(dt), keys, vals, offs, n, nseg, o.partition,
                      o.stop_after, o.debug_flags, o.fan_in, o.tile, o.merge, o.d_packet_offsets_out, ws,
-                     o.d_workspace ? o.workspace_bytes : need};
+                     o.d_workspace ? o.workspace_bytes : need, src};
   auto it = g_graphs.find(key);
   if (it == g_graphs.end()) {
     if (g_graphs.size() >= kMaxGraphs) {  // evict the least recently used graph
@@ -370,12 +373,24 @@ hs_status hs_sort_keys_host(hs_dtype dtype, void* h_keys, size_t n, const hs_opt
     std::lock_guard<std::mutex> lk(g_mu);
     HS_TRY(grow(g_stage, st, bytes, &d));
   }
-  cudaError_t e = cudaMemcpyAsync(d, h_keys, bytes, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) {
-    set_cuda_error(e);
-    return HS_ERR_CUDA;
+  // Pinned host memory that the device can address is read by the sort's
+  // first pass itself (the histogram copies the keys in while it counts
+  // them); other host memory is copied in first.
+  const void* src = nullptr;
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, h_keys) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+      pa.devicePointer != nullptr)
+    src = pa.devicePointer;  // an address of that memory the current device can load from
+  cudaGetLastError();  // a pageable pointer may leave an error behind
+  cudaError_t e = cudaSuccess;
+  if (!src) {
+    e = cudaMemcpyAsync(d, h_keys, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return HS_ERR_CUDA;
+    }
   }
-  hs_status s = hs_sort_keys(dtype, d, n, opts, stream);
+  hs_status s = dispatch(dtype, d, nullptr, n, 1, nullptr, opts, stream, src);
   if (s != HS_OK) return s;
   e = cudaMemcpyAsync(h_keys, d, bytes, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

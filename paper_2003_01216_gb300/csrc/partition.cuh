@@ -162,7 +162,11 @@ __device__ __forceinline__ uint32_t find_seg(const uint32_t* __restrict__ pre, u
 // (atomicMax) when the segment changes and at the end.
 //   img = 0: identity image (and every segment's "has a negative key" flag);
 //            the keys of block b+1 arrive by bulk copy into the other of two
-//            shared-memory stages while block b is counted
+//            shared-memory stages while block b is counted.  FROM_SRC (keys
+//            in pinned host memory that the device can address, at `src`):
+//            each block is read from src by plain loads and written to
+//            `keys` on the way: the copy into the device and the count are
+//            one pass.
 //   img = 1: sign-flipped image, only for blocks of segments flagged by the
 //            img = 0 pass (plain loads; the kernel returns at once when no
 //            segment holds a negative key)
@@ -170,7 +174,7 @@ __device__ __forceinline__ uint32_t find_seg(const uint32_t* __restrict__ pre, u
 template <class K, int NB, int BLOCK, int IPT>
 __device__ __forceinline__ void hist_count_block(const K* keysrc, uint32_t cnt, bool flip, int img,
                                                  uint32_t* s_cnt, typename KT<K>::U* s_max, uint32_t& s_neg,
-                                                 int& cls_out) {
+                                                 int& cls_out, K* copy_to = nullptr) {
   using U = typename KT<K>::U;
   constexpr int NW = BLOCK / kWarp;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -178,11 +182,25 @@ __device__ __forceinline__ void hist_count_block(const K* keysrc, uint32_t cnt, 
   U u[IPT];
   U m = 0;
   const bool full = cnt == static_cast<uint32_t>(BLOCK * IPT);
+  if (copy_to) {  // keys read from host memory are also written to the device array
 #pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
-    u[j] = (full || i < cnt) ? KT<K>::image(keysrc[i], flip) : U(0);
-    m = max(m, u[j]);
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
+      u[j] = U(0);
+      if (full || i < cnt) {
+        const K x = keysrc[i];
+        copy_to[i] = x;
+        u[j] = KT<K>::image(x, flip);
+      }
+      m = max(m, u[j]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
+      u[j] = (full || i < cnt) ? KT<K>::image(keysrc[i], flip) : U(0);
+      m = max(m, u[j]);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, static_cast<U>(__shfl_xor_sync(0xffffffffu, m, o)));
@@ -226,8 +244,8 @@ __device__ __forceinline__ void hist_count_block(const K* keysrc, uint32_t cnt, 
   __syncthreads();
 }
 
-template <class K, int NB, int BLOCK, int IPT>
-__global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint32_t nseg, uint32_t part_tile,
+template <class K, int NB, int BLOCK, int IPT, bool FROM_SRC = false>
+__global__ void __launch_bounds__(BLOCK) k_hist(K* keys, const K* __restrict__ src, uint32_t nseg, uint32_t part_tile,
                                                  int img, Tables tb) {
   griddep_open();
   using U = typename KT<K>::U;
@@ -291,7 +309,9 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
     }
   };
 
-  if (img == 0 && wid == NW - 1) issue(b0, 0);
+  // keys in host memory (src): plain loads, no bulk copies
+  const bool from_src = FROM_SRC && img == 0;
+  if (img == 0 && !from_src && wid == NW - 1) issue(b0, 0);
   uint32_t par0 = 0, par1 = 0;
   int st = 0;
   for (uint32_t b = b0; b < b1; ++b) {
@@ -302,7 +322,14 @@ __global__ void __launch_bounds__(BLOCK) k_hist(const K* __restrict__ keys, uint
     const uint64_t beg = tb.seg_off[seg] + static_cast<uint64_t>(b - tb.blk_prefix[seg]) * part_tile;
     const uint32_t cnt = static_cast<uint32_t>(min64(part_tile, tb.seg_off[seg + 1] - beg));
     int cls = 0;
-    if (img == 0) {
+    if constexpr (FROM_SRC) {
+      if (img == 0) {
+        hist_count_block<K, NB, BLOCK, IPT>(src + beg, cnt, false, 0, s_cnt, s_max, s_neg, cls, keys + beg);
+      } else {
+        if (!tb.seg_neg[seg]) continue;  // block-uniform
+        hist_count_block<K, NB, BLOCK, IPT>(keys + beg, cnt, true, 1, s_cnt, s_max, s_neg, cls);
+      }
+    } else if (img == 0) {
       if (wid == NW - 1 && b + 1 < b1) issue(b + 1, st ^ 1);
       const uint32_t ph = st ? par1 : par0;
       const bool ok = mbar_wait_bounded(&s_bar[st], ph, tb.err, 2000000000ull);

@@ -90,11 +90,12 @@ class Launcher {
     }
     return end(false);
   }
-  hs_status copy(const char* name, void* dst, const void* src, size_t bytes) {
+  hs_status copy(const char* name, void* dst, const void* src, size_t bytes,
+                 cudaMemcpyKind kind = cudaMemcpyDeviceToDevice) {
     if (!bytes) return HS_OK;
     prev_kernel_ = false;
     begin(name);
-    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st_);
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, st_);
     if (e != cudaSuccess) {
       set_cuda_error(e);
       return HS_ERR_CUDA;
@@ -111,9 +112,11 @@ class Launcher {
 
 // Entry points of the per-(key type, tile shape) translation units
 // (sort_shape.cu): run_sort_<key>_t<items per thread>.
+// `src`: nullptr, or the keys in pinned host memory the device can address
+// (hs_sort_keys_host): the sort then reads them from there into `keys`.
 #define HS_SORT_SHAPE_DECL(name)                                                                            \
   hs_status name(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o, \
-                 char* ws, uint32_t* err, cudaStream_t st)
+                 char* ws, uint32_t* err, cudaStream_t st, const void* src)
 HS_SORT_SHAPE_DECL(run_sort_i32_t11);
 HS_SORT_SHAPE_DECL(run_sort_i32_t15);
 HS_SORT_SHAPE_DECL(run_sort_i32_t23);

@@ -102,14 +102,40 @@ def test_caller_workspace(oracle):
         hs.sort_keys(tk, workspace=big[16:16 + need])
 
 
-def test_host_buffers(oracle):
-    keys = I.generate("uniform1e9", 200_000, seed=12)
-    h = keys.copy()
-    hs.sort_keys_host(h)
-    assert_equal(h, oracle.sort(keys)[0], "host-buffer sort")
-    pinned = torch.from_numpy(keys.copy()).pin_memory()
-    hs.sort_keys_host(pinned)
-    assert_equal(pinned.numpy(), oracle.sort(keys)[0], "pinned host-buffer sort")
+# (distribution, n, partition): pinned memory is read by the histogram kernel
+# itself (several blocks per CTA, a ragged last block; negative int32 keys
+# also take the flipped-image pass, which then reads the device copy); with
+# partition 1 or n of at most one tile there is no histogram and the sort
+# copies the keys in first
+HOST_CASES = [("uniform1e9", 200_000, 10), ("int32full", 1_500_001, 10), ("uniform64", 777_777, 10),
+              ("uniform32", 300_003, 256), ("zipf", 250_000, 1), ("uniform31", 5_000, 10), ("uniform64", 1, 10)]
+
+
+@pytest.mark.parametrize("dist,n,nb", HOST_CASES, ids=[f"{d}-{n}-{nb}" for d, n, nb in HOST_CASES])
+def test_host_buffers(oracle, dist, n, nb):
+    keys = I.generate(dist, n, seed=12)
+    exp = oracle.sort(keys, nbuckets=nb)[0]
+    h = keys.copy()  # pageable: copied in by cudaMemcpyAsync
+    hs.sort_keys_host(h, partition=nb)
+    assert_equal(h, exp, "host-buffer sort")
+    pinned = torch.from_numpy(keys.copy()).pin_memory()  # device-addressable: read by the sort itself
+    for _ in range(2):  # the second call sorts sorted keys, same result
+        hs.sort_keys_host(pinned, partition=nb)
+        assert hs.stream_error() == 0
+        assert_equal(pinned.numpy(), exp, "pinned host-buffer sort")
+    # which path ran: the histogram that reads host memory, or a copy in
+    pinned.copy_(torch.from_numpy(keys))
+    hs.timing_read()
+    hs.timing_enable(True)
+    try:
+        hs.sort_keys_host(pinned, partition=nb)
+        names = set(hs.timing_read())
+    finally:
+        hs.timing_enable(False)
+    assert_equal(pinned.numpy(), exp, "pinned host-buffer sort, timed")
+    code = {np.dtype(np.int32): 0, np.dtype(np.uint32): 1, np.dtype(np.uint64): 2}[keys.dtype]
+    fused = nb != 1 and n > hs.plan(code, n)["tile"]
+    assert ("hist_copy_in" in names) == fused and ("copy_in" in names) == (not fused), sorted(names)
 
 
 def test_streams_do_not_share_work_space(oracle):
