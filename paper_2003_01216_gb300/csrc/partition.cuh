@@ -171,6 +171,48 @@ __device__ __forceinline__ uint32_t find_seg(const uint32_t* __restrict__ pre, u
 //            img = 0 pass (plain loads; the kernel returns at once when no
 //            segment holds a negative key)
 // ---------------------------------------------------------------------------
+// Decimal digit count of a 32-bit image (1..10), by comparisons with
+// immediate powers of ten.
+__device__ __forceinline__ int dec_class32(uint32_t v) {
+  return 1 + (v >= 10u) + (v >= 100u) + (v >= 1000u) + (v >= 10000u) + (v >= 100000u) + (v >= 1000000u) +
+         (v >= 10000000u) + (v >= 100000000u) + (v >= 1000000000u);
+}
+
+// The keys of one block: images into u[] (and the block maximum into m);
+// FULL: every item of the block exists (no bounds tests).
+template <class K, int BLOCK, int IPT, bool FULL>
+__device__ __forceinline__ void hist_load(const K* keysrc, uint32_t cnt, bool flip, K* copy_to,
+                                          typename KT<K>::U (&u)[IPT], typename KT<K>::U& m) {
+  using U = typename KT<K>::U;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
+    u[j] = U(0);
+    if (FULL || i < cnt) {
+      const K x = keysrc[i];
+      if (copy_to) copy_to[i] = x;  // keys read from host memory also go to the device array
+      u[j] = KT<K>::image(x, flip);
+    }
+    m = max(m, u[j]);
+  }
+}
+
+// Ten packets: packed per-thread counters, 4 bits per packet (a thread holds
+// at most IPT <= 15 keys), packets 0..7 in `lo`, 8..9 in `hi`.
+template <class U, int IPT, bool FULL>
+__device__ __forceinline__ void hist_count10(const U (&u)[IPT], uint32_t cnt, const DigitRule& rule, uint32_t& lo,
+                                             uint32_t& hi) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
+    const uint32_t p = packet_of<10>(u[j], rule);
+    const uint32_t inc = (FULL || i < cnt) ? (1u << (4 * (p & 7))) : 0u;
+    if (p < 8) lo += inc; else hi += inc;
+  }
+}
+
 template <class K, int NB, int BLOCK, int IPT>
 __device__ __forceinline__ void hist_count_block(const K* keysrc, uint32_t cnt, bool flip, int img,
                                                  uint32_t* s_cnt, typename KT<K>::U* s_max, uint32_t& s_neg,
@@ -182,26 +224,8 @@ __device__ __forceinline__ void hist_count_block(const K* keysrc, uint32_t cnt, 
   U u[IPT];
   U m = 0;
   const bool full = cnt == static_cast<uint32_t>(BLOCK * IPT);
-  if (copy_to) {  // keys read from host memory are also written to the device array
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
-      u[j] = U(0);
-      if (full || i < cnt) {
-        const K x = keysrc[i];
-        copy_to[i] = x;
-        u[j] = KT<K>::image(x, flip);
-      }
-      m = max(m, u[j]);
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
-      u[j] = (full || i < cnt) ? KT<K>::image(keysrc[i], flip) : U(0);
-      m = max(m, u[j]);
-    }
-  }
+  if (full) hist_load<K, BLOCK, IPT, true>(keysrc, cnt, flip, copy_to, u, m);
+  else hist_load<K, BLOCK, IPT, false>(keysrc, cnt, flip, copy_to, u, m);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, static_cast<U>(__shfl_xor_sync(0xffffffffu, m, o)));
   if (lane == 0) s_max[wid] = m;
@@ -211,26 +235,26 @@ __device__ __forceinline__ void hist_count_block(const K* keysrc, uint32_t cnt, 
   for (int w = 1; w < NW; ++w) m = max(m, s_max[w]);
   // int32 under the identity image: a negative key is an image with the top bit set
   if (std::is_same<K, int32_t>::value && img == 0 && tid == 0 && (static_cast<uint64_t>(m) >> 31)) s_neg = 1;
-  const int cls = (NB == 10) ? dec_class(m) : bin_class(m);
+  int cls;
+  if constexpr (NB == 10) cls = (sizeof(U) == 4) ? dec_class32(static_cast<uint32_t>(m)) : dec_class(m);
+  else cls = bin_class(m);
   const DigitRule rule = (NB == 10) ? rule_dec(cls) : make_rule_bin(cls);
   if constexpr (NB == 10) {
-    // packed per-thread counters, 4 bits per packet (a thread holds at most
-    // IPT <= 15 keys): packets 0..7 in `lo`, 8..9 in `hi`
     static_assert(IPT <= 15, "4-bit counters");
     uint32_t lo = 0, hi = 0;
+    if (full) hist_count10<U, IPT, true>(u, cnt, rule, lo, hi);
+    else hist_count10<U, IPT, false>(u, cnt, rule, lo, hi);
+    // warp sums, two packets per reduction (16-bit fields: a warp counts at
+    // most 32 x 15 keys), then lane q adds packet q's sum to the block count
+    uint32_t mine = 0;
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const uint32_t i = wid * kWarp * IPT + j * kWarp + lane;
-      const uint32_t p = packet_of<NB>(u[j], rule);
-      const uint32_t inc = (full || i < cnt) ? (1u << (4 * (p & 7))) : 0u;
-      if (p < 8) lo += inc; else hi += inc;
+    for (int k = 0; k < 5; ++k) {
+      const uint32_t w0 = ((k < 4 ? lo : hi) >> (8 * (k & 3))) & 15u;
+      const uint32_t w1 = ((k < 4 ? lo : hi) >> (8 * (k & 3) + 4)) & 15u;
+      const uint32_t r = __reduce_add_sync(0xffffffffu, w0 | (w1 << 16));
+      if ((lane >> 1) == k) mine = (r >> (16 * (lane & 1))) & 0xffffu;
     }
-#pragma unroll
-    for (int q = 0; q < 10; ++q) {
-      const uint32_t field = ((q < 8 ? lo : hi) >> (4 * (q & 7))) & 15u;
-      const uint32_t c = __reduce_add_sync(0xffffffffu, field);
-      if (lane == 0 && c) atomicAdd(&s_cnt[q], c);
-    }
+    if (lane < 10 && mine) atomicAdd(&s_cnt[lane], mine);
   } else {
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
