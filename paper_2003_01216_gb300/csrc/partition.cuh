@@ -862,10 +862,13 @@ __global__ void __launch_bounds__(BLOCK, 2) k_scatter(const K* __restrict__ keys
 // ---------------------------------------------------------------------------
 // k_scatter_small: the stable move for up to 16 packets (the ten decimal
 // packets), persistent CTAs over blocks blockIdx.x, +gridDim.x, ...
-//   * a block's keys (and values) arrive by bulk copy in the CTA's input stage;
-//     thread t takes items t*IPT .. t*IPT+IPT-1 (so input order is thread
-//     order, then item order) and, once every thread holds its items, the next
-//     block's copy is issued into the same stage;
+//   * a block's keys (and values) arrive by bulk copy in one of the CTA's
+//     input stages; thread t takes items t*IPT .. t*IPT+IPT-1 (so input order
+//     is thread order, then item order).  With two stages the next block's
+//     copy is issued as soon as this block's has landed (into the stage the
+//     previous block was read from); with one (64-bit keys with values, where
+//     a second stage would halve the CTAs per SM) once every thread holds its
+//     items;
 //   * each thread counts its items per packet in 4-bit fields (its local rank
 //     of every item falls out on the way), and one block-wide scan of those
 //     counts, two packets per 32-bit word, gives every thread its first rank
@@ -880,17 +883,18 @@ __global__ void __launch_bounds__(BLOCK, 2) k_scatter(const K* __restrict__ keys
 template <class K, bool HAS_V, int BLOCK, int IPT>
 struct ScatterSmallLayout {
   static constexpr int TILE = BLOCK * IPT;
+  static constexpr int STAGES = (sizeof(K) == 8 && HAS_V) ? 1 : 2;
   static constexpr size_t SK = (region_elems(TILE) * sizeof(K) + 127) & ~size_t(127);
   static constexpr size_t SV = HAS_V ? ((region_elems(TILE) * 4 + 127) & ~size_t(127)) : 0;
   static constexpr int OUTE = TILE + 8 * 16;  // runs padded to their phase: at most 7 extra per run
   static constexpr size_t OK = (OUTE * sizeof(K) + 127) & ~size_t(127);
   static constexpr size_t OV = HAS_V ? ((OUTE * 4 + 127) & ~size_t(127)) : 0;
   static constexpr size_t PREF = BLOCK * 16 * 2;  // u16 first staging position per thread and packet
-  static constexpr size_t bytes = SK + SV + OK + OV + PREF;
+  static constexpr size_t bytes = STAGES * (SK + SV) + OK + OV + PREF;
 };
 
 // Register budget: four CTAs per SM for 4-byte keys without values (64
-// registers; its shared memory, ~40 KB, fits four times under the largest
+// registers; its shared memory, ~54 KB, fits four times under the largest
 // carveout, which the launch requests), two otherwise.
 template <class K, bool HAS_V, int NB, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_scatter_small(const K* __restrict__ keys_in,
@@ -902,23 +906,27 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_sc
   using LY = ScatterSmallLayout<K, HAS_V, BLOCK, IPT>;
   constexpr int NW = BLOCK / kWarp;
   constexpr int NWORD = (NB + 1) / 2;
+  constexpr int ST = LY::STAGES;
   extern __shared__ __align__(128) unsigned char s_raw[];
-  K* s_in = reinterpret_cast<K*>(s_raw);
-  uint32_t* s_inv = reinterpret_cast<uint32_t*>(s_raw + LY::SK);
-  K* s_out = reinterpret_cast<K*>(s_raw + LY::SK + LY::SV);
-  uint32_t* s_outv = reinterpret_cast<uint32_t*>(s_raw + LY::SK + LY::SV + LY::OK);
-  uint16_t* s_pref = reinterpret_cast<uint16_t*>(s_raw + LY::SK + LY::SV + LY::OK + LY::OV);
+  auto s_in = [&](int st) { return reinterpret_cast<K*>(s_raw + st * LY::SK); };
+  auto s_inv = [&](int st) { return reinterpret_cast<uint32_t*>(s_raw + ST * LY::SK + st * LY::SV); };
+  K* s_out = reinterpret_cast<K*>(s_raw + ST * (LY::SK + LY::SV));
+  uint32_t* s_outv = reinterpret_cast<uint32_t*>(s_raw + ST * (LY::SK + LY::SV) + LY::OK);
+  uint16_t* s_pref = reinterpret_cast<uint16_t*>(s_raw + ST * (LY::SK + LY::SV) + LY::OK + LY::OV);
   __shared__ uint32_t s_wsum[NW][NWORD];
   __shared__ uint32_t s_blk[NWORD];
   __shared__ uint32_t s_run[NB], s_tot[NB], s_dst[NB], s_pe[NB];
-  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_bar[2];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
   const uint32_t total = tb.blk_prefix[nseg];
   const uint32_t G = gridDim.x;
   uint32_t b = blockIdx.x;
   if (b >= total) return;
-  if (tid == 0) mbar_init(&s_bar, 1);
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+  }
   mbar_fence_init();
   __syncthreads();
 
@@ -927,21 +935,21 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_sc
     beg = tb.seg_off[sg] + static_cast<uint64_t>(bb - tb.blk_prefix[sg]) * part_tile;
     cnt = static_cast<uint32_t>(min64(part_tile, tb.seg_off[sg + 1] - beg));
   };
-  auto issue = [&](uint32_t bb) {  // one warp (the last)
+  auto issue = [&](uint32_t bb, int st) {  // one warp (the last)
     uint32_t sg, c;
     uint64_t bg;
     geom(bb, sg, bg, c);
     if (lane == 0) fence_proxy_async();  // the generic reads of the stage happened before the last barrier
     __syncwarp();
-    const PendingBulk<K> pk = load_window_singles(s_in, phase_of(keys_in + bg), keys_in + bg, c, lane);
+    const PendingBulk<K> pk = load_window_singles(s_in(st), phase_of(keys_in + bg), keys_in + bg, c, lane);
     PendingBulk<uint32_t> pv{nullptr, nullptr, 0};
-    if constexpr (HAS_V) pv = load_window_singles(s_inv, phase_of(vals_in + bg), vals_in + bg, c, lane);
-    cp_async_mbar_arrive(&s_bar);
+    if constexpr (HAS_V) pv = load_window_singles(s_inv(st), phase_of(vals_in + bg), vals_in + bg, c, lane);
+    cp_async_mbar_arrive(&s_bar[st]);
     __syncwarp();
     if (lane == 0) {
-      mbar_arrive_expect_tx(&s_bar, pk.bytes + pv.bytes);
-      if (pk.bytes) bulk_g2s(pk.sdst, pk.gsrc, pk.bytes, &s_bar);
-      if (HAS_V && pv.bytes) bulk_g2s(pv.sdst, pv.gsrc, pv.bytes, &s_bar);
+      mbar_arrive_expect_tx(&s_bar[st], pk.bytes + pv.bytes);
+      if (pk.bytes) bulk_g2s(pk.sdst, pk.gsrc, pk.bytes, &s_bar[st]);
+      if (HAS_V && pv.bytes) bulk_g2s(pv.sdst, pv.gsrc, pv.bytes, &s_bar[st]);
     }
   };
   // absolute first position and packet end of every packet of block bb (threads < NB)
@@ -953,23 +961,27 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_sc
   };
 
   constexpr int kIssueWarp = NW - 1;  // warp 0 computes the run offsets
-  if (wid == kIssueWarp) issue(b);
+  if (wid == kIssueWarp) issue(b, 0);
   uint32_t nd = 0, npe = 0;
   if (tid < NB) load_dst(b, nd, npe);
-  uint32_t parity = 0;
+  uint32_t par0 = 0, par1 = 0;
+  int st = 0;
   bool failed = false;
   for (; b < total; b += G) {
     uint32_t seg, cnt;
     uint64_t beg;
     geom(b, seg, beg, cnt);
-    const bool ok = mbar_wait_bounded(&s_bar, parity, tb.err, kWaitNs);
-    parity ^= 1;
+    const bool ok = mbar_wait_bounded(&s_bar[st], st ? par1 : par0, tb.err, kWaitNs);
+    if (st) par1 ^= 1; else par0 ^= 1;
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
     }
     // after the barrier: every warp has finished the previous block's stores,
-    // which read s_dst and s_pe
+    // which read s_dst and s_pe, and its reads of the other stage
+    if constexpr (ST == 2) {
+      if (wid == kIssueWarp && b + G < total) issue(b + G, st ^ 1);  // refill the other stage now
+    }
     if (tid < NB) {
       s_dst[tid] = nd;
       s_pe[tid] = npe;
@@ -978,8 +990,8 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_sc
     const bool flip = tb.seg_flip[seg] != 0;
     const DigitRule rule = (NB == 10) ? rule_dec(static_cast<int>(tb.seg_class[seg]))
                                       : make_rule_bin(static_cast<int>(tb.seg_class[seg]));
-    const K* rk = s_in + phase_of(keys_in + beg);
-    const uint32_t* rv = HAS_V ? s_inv + phase_of(vals_in + beg) : nullptr;
+    const K* rk = s_in(st) + phase_of(keys_in + beg);
+    const uint32_t* rv = HAS_V ? s_inv(st) + phase_of(vals_in + beg) : nullptr;
     K k[IPT];
     uint32_t v[IPT];
     uint32_t pr[IPT];  // packet in bits 0..7 (NB = none), local rank from bit 8
@@ -1004,8 +1016,10 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_sc
         else pr[j] = NB;
       }
     }
-    __syncthreads();  // every item is in registers: the stage may be refilled
-    if (wid == kIssueWarp && b + G < total) issue(b + G);
+    if constexpr (ST == 1) {
+      __syncthreads();  // every item is in registers: the stage may be refilled
+      if (wid == kIssueWarp && b + G < total) issue(b + G, 0);
+    }
     // local counts, two packets per word, and their block-wide scan
     uint32_t wv[NWORD], incl[NWORD];
 #pragma unroll
@@ -1087,10 +1101,12 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_sc
       stored = true;
     }
     if (stored && lane == 0) bulk_commit();
+    if constexpr (ST == 2) st ^= 1;
   }
-  // the copy that did not arrive may still be in flight into the stage: give
-  // it a bounded chance to land before the CTA's shared memory is released
-  if (failed) mbar_wait_bounded(&s_bar, parity ^ 1u, tb.err, kWaitNs);
+  // the copy that did not arrive may still be in flight into its stage (the
+  // next block's copy is issued only after the barrier that saw the failure):
+  // give it a bounded chance to land before the CTA's shared memory is released
+  if (failed) mbar_wait_bounded(&s_bar[st], st ? par1 ^ 1u : par0 ^ 1u, tb.err, kWaitNs);
   if (lane == 0) bulk_wait0();
 }
 
