@@ -615,6 +615,17 @@ def run_batch(args, rank, world, dev, dist_name):
         }), flush=True)
 
 
+def serve_warm_up(serve) -> None:
+    """One pass of requests at all the sizes and key types a serving run meets
+    (lengths 2^10 .. 2^26, int32 and uint64), through the server (batches and
+    single sorts) and through the serial per-request path."""
+    sizes = [1 << e for e in range(10, 27, 2)]
+    warm = [serve.Request(i, 0.0, code, n) for i, (code, n) in enumerate((c, n) for c in (0, 2) for n in sizes)]
+    serve.Server(slots=8, seed=99).run(warm)
+    serve.Server(slots=8, seed=99).run(serve.make_requests(1000.0, 0.02, 1024, 1 << 22, seed=99))
+    serve.serial(warm[::2], seed=99)
+
+
 def serve_measure(dev, rate: float, duration: float, serial_too: bool = True, seed: int = 0) -> dict:
     """Config 5: Poisson arrivals at `rate` for `duration` seconds, int32 or
     uint64 (50/50), lengths log-uniform in [1024, 2^26], 64 GB HBM budget,
@@ -625,9 +636,11 @@ def serve_measure(dev, rate: float, duration: float, serial_too: bool = True, se
 
     reqs = serve.make_requests(rate, duration, 1024, 1 << 26, seed=seed)
     offered = sum(r.n for r in reqs) / duration
-    # warm up: the kernels and the caching allocator see each path once
-    warm = serve.make_requests(1000.0, 0.02, 1024, 1 << 22, seed=99)
-    serve.Server(slots=8, seed=99).run(warm)
+    # warm up: every kernel the stream can reach (both key types, single
+    # sorts of every size class up to the largest request, batches of small
+    # ones) is loaded and its launch shape set up, and the caching allocator
+    # holds blocks of every size, before the timed region
+    serve_warm_up(serve)
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
         clk.mark()
