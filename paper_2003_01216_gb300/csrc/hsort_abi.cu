@@ -378,10 +378,11 @@ hs_status hs_sort_keys_host(hs_dtype dtype, void* h_keys, size_t n, const hs_opt
   // them); other host memory is copied in first.
   const void* src = nullptr;
   cudaPointerAttributes pa{};
-  if (cudaPointerGetAttributes(&pa, h_keys) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-      pa.devicePointer != nullptr)
+  const cudaError_t ea = cudaPointerGetAttributes(&pa, h_keys);
+  if (ea == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr)
     src = pa.devicePointer;  // an address of that memory the current device can load from
-  cudaGetLastError();  // a pageable pointer may leave an error behind
+  else if (ea != cudaSuccess)
+    cudaGetLastError();  // the query's own error (older runtimes reject unregistered pointers): not the caller's
   cudaError_t e = cudaSuccess;
   if (!src) {
     e = cudaMemcpyAsync(d, h_keys, bytes, cudaMemcpyHostToDevice, st);
