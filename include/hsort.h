@@ -92,11 +92,13 @@ typedef struct {
                            256-byte aligned (else HS_ERR_INVALID); when set, the library
                            allocates nothing for this call */
   size_t workspace_bytes;
-  int debug_flags;      /* testing only: bit 0 = one bulk copy announces 16 bytes that never
-                           arrive and the wait limit is shortened, so a bounded wait expires;
-                           bit 1 = in the persistent merge launch, the first merge block never
-                           publishes its completion and the wait limit is shortened, so the
-                           blocks that read its run give up (HS_ERR_TIMEOUT) */
+  int debug_flags;      /* testing only: bit 0 = one bulk copy of the tile sort announces 16
+                           bytes that never arrive and the wait limit is shortened, so a
+                           bounded wait expires; bit 1 = in the persistent merge launch, the
+                           first merge block never publishes its completion and the wait limit
+                           is shortened, so the blocks that read its run give up; bit 2 = as
+                           bit 0, for a bulk copy of the packet step's scatter (ten packets).
+                           Each reports HS_ERR_TIMEOUT (the keys are then unspecified) */
   int graph;            /* 1 = capture this call's whole launch sequence in a CUDA graph the
                            first time these exact arguments (pointers, sizes, options, stream)
                            are seen, and replay the instantiated graph on later calls.  Needs a

@@ -350,8 +350,10 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         grid = persistent_grid(kern, kBlock, smem);
       }
+      const bool stuck = (o.debug_flags & 4) != 0;
+      const uint64_t limit_ns = stuck ? 2000000ull : 2000000000ull;  // 2 ms when injected, else 2 s
       HS_TRY(lc.kernel("scatter", kern, capped(grid, L.max_blocks), kBlock, smem, keys, vals, kw, vw, nseg32, kTile,
-                       tb));
+                       stuck ? 1 : 0, limit_ns, tb));
     } else {
       const size_t smem = scatter_smem<K, HAS_V, NB>();
       auto kern = k_scatter<K, HAS_V, NB, kBlock, kIpt>;

@@ -900,7 +900,8 @@ template <class K, bool HAS_V, int NB, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_scatter_small(const K* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
                                                             K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                                                            uint32_t nseg, uint32_t part_tile, Tables tb) {
+                                                            uint32_t nseg, uint32_t part_tile, int debug_stuck,
+                                                            uint64_t limit_ns, Tables tb) {
   griddep_open();
   static_assert(NB <= 16 && IPT <= 15, "4-bit local counts; 16-bit block counts");
   using LY = ScatterSmallLayout<K, HAS_V, BLOCK, IPT>;
@@ -947,7 +948,10 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_sc
     cp_async_mbar_arrive(&s_bar[st]);
     __syncwarp();
     if (lane == 0) {
-      mbar_arrive_expect_tx(&s_bar[st], pk.bytes + pv.bytes);
+      // testing hook: CTA 0 announces 16 bytes that never arrive for its
+      // first block, so its bounded wait expires
+      const uint32_t extra = (debug_stuck && blockIdx.x == 0 && bb == blockIdx.x) ? 16u : 0u;
+      mbar_arrive_expect_tx(&s_bar[st], pk.bytes + pv.bytes + extra);
       if (pk.bytes) bulk_g2s(pk.sdst, pk.gsrc, pk.bytes, &s_bar[st]);
       if (HAS_V && pv.bytes) bulk_g2s(pv.sdst, pv.gsrc, pv.bytes, &s_bar[st]);
     }
@@ -971,7 +975,7 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_sc
     uint32_t seg, cnt;
     uint64_t beg;
     geom(b, seg, beg, cnt);
-    const bool ok = mbar_wait_bounded(&s_bar[st], st ? par1 : par0, tb.err, kWaitNs);
+    const bool ok = mbar_wait_bounded(&s_bar[st], st ? par1 : par0, tb.err, limit_ns);
     if (st) par1 ^= 1; else par0 ^= 1;
     if (__syncthreads_or(!ok)) {
       failed = true;
@@ -1106,7 +1110,7 @@ __global__ void __launch_bounds__(BLOCK, (HAS_V || sizeof(K) == 8) ? 2 : 4) k_sc
   // the copy that did not arrive may still be in flight into its stage (the
   // next block's copy is issued only after the barrier that saw the failure):
   // give it a bounded chance to land before the CTA's shared memory is released
-  if (failed) mbar_wait_bounded(&s_bar[st], st ? par1 ^ 1u : par0 ^ 1u, tb.err, kWaitNs);
+  if (failed) mbar_wait_bounded(&s_bar[st], st ? par1 ^ 1u : par0 ^ 1u, tb.err, limit_ns);
   if (lane == 0) bulk_wait0();
 }
 

@@ -87,6 +87,25 @@ def test_bounded_wait_expires_and_context_survives(oracle):
     assert_equal(gk, oracle.sort(keys)[0], "sort after an expired wait")
 
 
+def test_scatter_wait_expires_and_context_survives(oracle):
+    # the same for the packet step's scatter (two input stages): CTA 0's first
+    # block never completes its copy, its bounded wait gives up, and the copy
+    # of the next block was never issued, so nothing is left in flight
+    # (64-bit keys with values take the one-stage layout)
+    for dist, n, with_vals in (("uniform31", 1_000_000, False), ("uniform64", 300_000, False),
+                               ("uniform64", 300_000, True)):
+        keys = I.generate(dist, n, seed=10)
+        vals = I.index_values(n) if with_vals else None
+        _, _, _, st = run(keys, vals, debug_flags=4)
+        assert st == HS_TIMEOUT
+        gk, gv, _, st = run(keys, vals)
+        assert st == 0
+        ek, ev, _ = oracle.sort(keys, vals)
+        assert_equal(gk, ek, "sort after an expired scatter wait")
+        if with_vals:
+            assert_equal(gv, ev, "values after an expired scatter wait")
+
+
 def test_caller_workspace(oracle):
     keys = I.generate("zipf", 50_000, seed=11)
     need = hs.workspace_size(0, keys.size)
