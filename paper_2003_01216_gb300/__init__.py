@@ -101,7 +101,7 @@ def sort_batch(keys, offsets, vals=None, partition: int = 10, stop_after: int = 
     return keys
 
 
-def sort_keys_host(arr, partition: int = 10, stream=None, fan_in: int = 0):
+def sort_keys_host(arr, partition: int = 10, stream=None, fan_in: int = 0, merge: int = 0, tile: int = 0):
     """Sort host keys (numpy array or CPU tensor, contiguous) in place through
     the device; returns after the result is back in host memory."""
     import numpy as np
@@ -112,7 +112,7 @@ def sort_keys_host(arr, partition: int = 10, stream=None, fan_in: int = 0):
         if not arr.flags.c_contiguous:
             raise ValueError("array must be contiguous")
         ptr, n, code = arr.ctypes.data, arr.size, codes[arr.dtype]
-    o = N.make_opts(partition=partition, fan_in=fan_in)
+    o = N.make_opts(partition=partition, fan_in=fan_in, merge=merge, tile=tile)
     N.check(N.lib().hs_sort_keys_host(code, ptr, n, ctypes.byref(o), _stream(stream)), "hs_sort_keys_host")
     return arr
 

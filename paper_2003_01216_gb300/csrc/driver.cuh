@@ -254,9 +254,14 @@ hs_status launch_bound4(Launcher& lc, K* keys, K* kw, Rec4* recs, uint32_t* list
 // memory the device can address (one segment, no values): the histogram
 // reads them from there and writes them into `keys` in the same pass (a
 // call without a histogram copies them in first).
+// host_done (may be nullptr): set to 1 when the sorted keys were also
+// written back to `src` by the kernels (the merge queue writes every packet's
+// last pass there, and the packets with no merge pass are copied there);
+// otherwise 0 and the caller copies `keys` back.
 template <class K, bool HAS_V, int NB, int IPT>
 hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
-                      char* ws, uint32_t* err, cudaStream_t st, const K* src) {
+                      char* ws, uint32_t* err, cudaStream_t st, const K* src, int* host_done) {
+  if (host_done) *host_done = 0;
   const Layout L = make_layout(sizeof(K), n, HAS_V, nseg, NB);
   const int fan = o.fan_in == 4 ? 4 : 2;
   Tables tb = make_tables(ws, L, err, fan_log2_of(fan));
@@ -409,10 +414,12 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       }
     } else if (o.merge != kMergePerPass) {
       // every merge pass in one persistent launch (dependency-driven queue)
-      static PerDevice sgrid_cache;
+      static PerDevice sgrid_cache, hgrid_cache;
       int& sgrid = sgrid_cache();
+      int& hgrid = hgrid_cache();
       const size_t smem = 2 * merge_stage_bytes<K, HAS_V>(kBlock * IPT);  // two stages
       auto sk = k_merge_sched<K, HAS_V, kBlock, IPT>;
+      auto hk = k_merge_sched<K, HAS_V, kBlock, IPT, !HAS_V>;  // last passes to host memory (keys only)
       if (!sgrid) sgrid = persistent_grid(sk, kBlock + 32, smem);
       const bool drop = (o.debug_flags & 2) != 0;
       SchedArgs sa;
@@ -421,9 +428,24 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
       sa.pass_limit = o.stop_after >= 3 ? o.stop_after - 2 : kMaxPasses;
       sa.debug_drop = drop ? 1 : 0;
       sa.limit_ns = drop ? 2000000ull : 2000000000ull;  // 2 ms when a completion is dropped, else 2 s
+      // keys from host memory: every packet's last pass writes straight back
+      // to the caller's host array (no copy out after the sort)
+      const bool to_host = !HAS_V && src != nullptr && nseg == 1 && o.stop_after == 0;
+      sa.host_out = to_host ? const_cast<K*>(src) : nullptr;
       if (worst_passes(n, (kBlock * IPT)) > 0) {
-        HS_TRY(lc.kernel("merge_sched", sk, capped(sgrid, L.max_units), kBlock + 32, smem, keys, vals, kw, vw, L.npk,
-                         tb, sa));
+        if (to_host) {
+          if (!hgrid) hgrid = persistent_grid(hk, kBlock + 32, smem);
+          HS_TRY(lc.kernel("merge_sched", hk, capped(hgrid, L.max_units), kBlock + 32, smem, keys, vals, kw, vw,
+                           L.npk, tb, sa));
+        } else {
+          HS_TRY(lc.kernel("merge_sched", sk, capped(sgrid, L.max_units), kBlock + 32, smem, keys, vals, kw, vw,
+                           L.npk, tb, sa));
+        }
+        if (to_host) {
+          HS_TRY(lc.kernel("copy_unmerged", k_copy_unmerged<K>, L.npk, 256, 0, static_cast<const K*>(keys),
+                           const_cast<K*>(src), L.npk, tb));
+          if (host_done) *host_done = 1;
+        }
       }
     } else {
       // per-pass launches: a co-rank kernel, then a merge kernel
@@ -459,24 +481,27 @@ hs_status run_sort_nb(K* keys, uint32_t* vals, size_t n, size_t nseg, const uint
 // translation unit per (key type, IPT) (sort_shape.cu).
 template <class K, bool HAS_V, int IPT>
 hs_status run_sort_part(K* k, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
-                        char* ws, uint32_t* err, cudaStream_t st, const K* src) {
-  if (o.partition == 1) return run_sort_nb<K, HAS_V, 1, IPT>(k, vals, n, nseg, offs, o, ws, err, st, src);
-  if (o.partition == 256) return run_sort_nb<K, HAS_V, 256, IPT>(k, vals, n, nseg, offs, o, ws, err, st, src);
-  return run_sort_nb<K, HAS_V, 10, IPT>(k, vals, n, nseg, offs, o, ws, err, st, src);
+                        char* ws, uint32_t* err, cudaStream_t st, const K* src, int* host_done) {
+  if (o.partition == 1) return run_sort_nb<K, HAS_V, 1, IPT>(k, vals, n, nseg, offs, o, ws, err, st, src, host_done);
+  if (o.partition == 256)
+    return run_sort_nb<K, HAS_V, 256, IPT>(k, vals, n, nseg, offs, o, ws, err, st, src, host_done);
+  return run_sort_nb<K, HAS_V, 10, IPT>(k, vals, n, nseg, offs, o, ws, err, st, src, host_done);
 }
 
 template <class K, int IPT>
 hs_status run_sort_ipt(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
-                       char* ws, uint32_t* err, cudaStream_t st, const void* src) {
+                       char* ws, uint32_t* err, cudaStream_t st, const void* src, int* host_done) {
   K* k = static_cast<K*>(keys);
   const K* ks = static_cast<const K*>(src);
+  if (host_done) *host_done = 0;
   if (src && (vals || nseg != 1)) return HS_ERR_INVALID;  // host keys: one array, keys only
   if (vals) {
     if constexpr (ipt_built<K, true, IPT>())
-      return run_sort_part<K, true, IPT>(k, vals, n, nseg, offs, o, ws, err, st, nullptr);
+      return run_sort_part<K, true, IPT>(k, vals, n, nseg, offs, o, ws, err, st, nullptr, nullptr);
     else return HS_ERR_UNSUPPORTED;
   } else {
-    if constexpr (ipt_built<K, false, IPT>()) return run_sort_part<K, false, IPT>(k, vals, n, nseg, offs, o, ws, err, st, ks);
+    if constexpr (ipt_built<K, false, IPT>())
+      return run_sort_part<K, false, IPT>(k, vals, n, nseg, offs, o, ws, err, st, ks, host_done);
     else return HS_ERR_UNSUPPORTED;
   }
 }

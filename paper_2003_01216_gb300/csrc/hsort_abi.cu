@@ -68,6 +68,7 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   unsigned long long kernels = 0;
   unsigned long long stamp = 0;
+  int host_done = 0;  // the captured kernels write the sorted keys back to host memory
 };
 constexpr size_t kMaxGraphs = 64;
 std::map<GraphKey, GraphEntry> g_graphs;
@@ -172,29 +173,29 @@ int tuned_fan_in(int dtype, bool has_vals, int partition, size_t n) {
 
 // The per-(key type, tile shape) entry points of sort_shape.cu.
 hs_status run_shape(hs_dtype dt, int tile, void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs,
-                    const hs_opts& o, char* ws, uint32_t* err, cudaStream_t st, const void* src) {
+                    const hs_opts& o, char* ws, uint32_t* err, cudaStream_t st, const void* src, int* host_done) {
   const int ipt = tile / kBlock;
   switch (dt) {
     case HS_INT32:
       switch (ipt) {
-        case 11: return run_sort_i32_t11(keys, vals, n, nseg, offs, o, ws, err, st, src);
-        case 15: return run_sort_i32_t15(keys, vals, n, nseg, offs, o, ws, err, st, src);
-        case 23: return run_sort_i32_t23(keys, vals, n, nseg, offs, o, ws, err, st, src);
-        case 31: return run_sort_i32_t31(keys, vals, n, nseg, offs, o, ws, err, st, src);
+        case 11: return run_sort_i32_t11(keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
+        case 15: return run_sort_i32_t15(keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
+        case 23: return run_sort_i32_t23(keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
+        case 31: return run_sort_i32_t31(keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
       }
       break;
     case HS_UINT32:
       switch (ipt) {
-        case 11: return run_sort_u32_t11(keys, vals, n, nseg, offs, o, ws, err, st, src);
-        case 15: return run_sort_u32_t15(keys, vals, n, nseg, offs, o, ws, err, st, src);
-        case 23: return run_sort_u32_t23(keys, vals, n, nseg, offs, o, ws, err, st, src);
-        case 31: return run_sort_u32_t31(keys, vals, n, nseg, offs, o, ws, err, st, src);
+        case 11: return run_sort_u32_t11(keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
+        case 15: return run_sort_u32_t15(keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
+        case 23: return run_sort_u32_t23(keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
+        case 31: return run_sort_u32_t31(keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
       }
       break;
     default:
       switch (ipt) {
-        case 11: return run_sort_u64_t11(keys, vals, n, nseg, offs, o, ws, err, st, src);
-        case 15: return run_sort_u64_t15(keys, vals, n, nseg, offs, o, ws, err, st, src);
+        case 11: return run_sort_u64_t11(keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
+        case 15: return run_sort_u64_t15(keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
       }
       break;
   }
@@ -215,9 +216,12 @@ hs_status check_opts(const hs_opts* opts, hs_opts* o) {
 }
 
 // src: nullptr, or the keys in pinned host memory the device can address
-// (hs_sort_keys_host); `keys` is then the device array they are sorted in.
+// (hs_sort_keys_host); `keys` is then the device array they are sorted in,
+// and *host_done (when given) tells whether the sorted keys were also written
+// back to src by the call's kernels.
 hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs,
-                   const hs_opts* opts, void* stream, const void* src = nullptr) {
+                   const hs_opts* opts, void* stream, const void* src = nullptr, int* host_done = nullptr) {
+  if (host_done) *host_done = 0;
   if (dt != HS_INT32 && dt != HS_UINT32 && dt != HS_UINT64) return HS_ERR_INVALID;
   hs_opts o;
   HS_TRY(check_opts(opts, &o));
@@ -259,7 +263,7 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
   }
   auto run = [&]() -> hs_status {
     switch (dt) {
-      default: return run_shape(dt, o.tile, keys, vals, n, nseg, offs, o, ws, err, st, src);
+      default: return run_shape(dt, o.tile, keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
     }
   };
   if (!o.graph || st == nullptr || timing_on()) return run();
@@ -298,8 +302,9 @@ hs_status dispatch(hs_dtype dt, void* keys, uint32_t* vals, size_t n, size_t nse
       return HS_ERR_CUDA;
     }
     g_launches.fetch_sub(kernels);  // captured, not launched: counted when replayed
-    it = g_graphs.emplace(key, GraphEntry{exec, kernels, 0}).first;
+    it = g_graphs.emplace(key, GraphEntry{exec, kernels, 0, host_done ? *host_done : 0}).first;
   }
+  if (host_done) *host_done = it->second.host_done;
   it->second.stamp = ++g_graph_clock;
   cudaError_t e = cudaGraphLaunch(it->second.exec, st);
   if (e != cudaSuccess) {
@@ -391,9 +396,12 @@ hs_status hs_sort_keys_host(hs_dtype dtype, void* h_keys, size_t n, const hs_opt
       return HS_ERR_CUDA;
     }
   }
-  hs_status s = dispatch(dtype, d, nullptr, n, 1, nullptr, opts, stream, src);
+  int host_done = 0;
+  hs_status s = dispatch(dtype, d, nullptr, n, 1, nullptr, opts, stream, src, &host_done);
   if (s != HS_OK) return s;
-  e = cudaMemcpyAsync(h_keys, d, bytes, cudaMemcpyDeviceToHost, st);
+  // the kernels wrote the result back themselves (merge passes in one
+  // persistent launch), or it is copied back now
+  if (!host_done) e = cudaMemcpyAsync(h_keys, d, bytes, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     set_cuda_error(e);

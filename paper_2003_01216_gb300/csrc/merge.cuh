@@ -18,6 +18,7 @@ struct MergeRec {
   uint32_t lb;   // B items merged by the block (la + lb = outputs; 0 = nothing to do)
 };
 constexpr uint64_t kSrcW = 1ull << 63;
+constexpr uint64_t kFinal = 1ull << 62;  // merge queue: the block is in its packet's last pass
 
 // Number of A items among the first `diag` outputs of merging A[0, la) and
 // B[0, lb) with A first on ties, for two diagonals at once (two independent
@@ -146,7 +147,7 @@ template <class K, bool HAS_V>
 __device__ __forceinline__ void merge_issue(const MergeRec& rec, K* rk, uint32_t* rv, uint64_t* bar, const K* ku,
                                             const uint32_t* vu, const K* kw, const uint32_t* vw, int lane) {
   const bool srcw = (rec.a & kSrcW) != 0;
-  const uint64_t a = rec.a & ~kSrcW;
+  const uint64_t a = rec.a & ~(kSrcW | kFinal);
   const K* ks = srcw ? kw : ku;
   uint32_t pa, pb;
   place2(ks + a, rec.la, ks + rec.b, pa, pb);

@@ -113,10 +113,12 @@ class Launcher {
 // Entry points of the per-(key type, tile shape) translation units
 // (sort_shape.cu): run_sort_<key>_t<items per thread>.
 // `src`: nullptr, or the keys in pinned host memory the device can address
-// (hs_sort_keys_host): the sort then reads them from there into `keys`.
+// (hs_sort_keys_host): the sort then reads them from there into `keys`, and
+// sets *host_done (when given) to 1 if it also wrote the sorted keys back
+// there (else the caller copies `keys` back).
 #define HS_SORT_SHAPE_DECL(name)                                                                            \
   hs_status name(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o, \
-                 char* ws, uint32_t* err, cudaStream_t st, const void* src)
+                 char* ws, uint32_t* err, cudaStream_t st, const void* src, int* host_done)
 HS_SORT_SHAPE_DECL(run_sort_i32_t11);
 HS_SORT_SHAPE_DECL(run_sort_i32_t15);
 HS_SORT_SHAPE_DECL(run_sort_i32_t23);

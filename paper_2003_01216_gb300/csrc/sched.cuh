@@ -132,9 +132,14 @@ struct SchedArgs {
   int pass_limit;       // passes to run (testing: stop after pass r), else kMaxPasses
   int debug_drop;       // testing: the block of ticket 0 never publishes its completion
   uint64_t limit_ns;    // bound of every wait
+  void* host_out;       // keys only: nullptr, or the caller's pinned host array (device-addressable):
+                        // blocks of a packet's last pass are written there instead of to U
 };
 
-template <class K, bool HAS_V, int BLOCK, int IPT>
+// TO_HOST (keys only, host-buffer calls): the blocks of a packet's last pass
+// are written to sa.host_out instead of U; a separate instantiation, so the
+// device-only kernel carries none of it.
+template <class K, bool HAS_V, int BLOCK, int IPT, bool TO_HOST = false>
 __global__ void __launch_bounds__(BLOCK + 32, (HAS_V || sizeof(K) == 8) ? 2 : 3)
     k_merge_sched(K* ku, uint32_t* vu, K* kw, uint32_t* vw, uint32_t npk, Tables tb, SchedArgs sa) {
   griddep_open();
@@ -288,7 +293,9 @@ __global__ void __launch_bounds__(BLOCK + 32, (HAS_V || sizeof(K) == 8) ? 2 : 3)
           if (!mbar_wait_sleepy(&s_rempty[slot], ((k / R) & 1) ^ 1, tb.err, sa.limit_ns, pub)) {
             ok = false;
           } else {
-            s_rec[slot] = make_rec(g, srcw, i0, i1);
+            MergeRec rec = make_rec(g, srcw, i0, i1);
+            if (TO_HOST && r == g.passes) rec.a |= kFinal;
+            s_rec[slot] = rec;
             s_sig[slot] = (sa.debug_drop && t == 0) ? kSigNone : sig;
             s_tkt[slot] = 0;
             mbar_arrive(&s_rfull[slot]);
@@ -429,7 +436,8 @@ __global__ void __launch_bounds__(BLOCK + 32, (HAS_V || sizeof(K) == 8) ? 2 : 3)
     K* rk = reinterpret_cast<K*>(s_raw + s * SB);
     uint32_t* rv = reinterpret_cast<uint32_t*>(s_raw + s * SB + KB);
     const bool srcw = (cur.a & kSrcW) != 0;
-    const uint64_t a = cur.a & ~kSrcW;
+    const bool to_host = TO_HOST && !HAS_V && (cur.a & kFinal) != 0;
+    const uint64_t a = cur.a & ~(kSrcW | kFinal);
     const K* ks = srcw ? kw : ku;
     uint32_t pa, pb;
     place2(ks + a, cur.la, ks + cur.b, pa, pb);
@@ -467,8 +475,33 @@ __global__ void __launch_bounds__(BLOCK + 32, (HAS_V || sizeof(K) == 8) ? 2 : 3)
     }
     fence_proxy_async();
     consumers_sync(BLOCK);
+    if constexpr (TO_HOST) {
+      if (to_host) {  // consumer-uniform
+        // the block's outputs are final: every consumer thread writes its
+        // share of the staged block to the host array by plain coalesced
+        // stores, and the stage is read completely before warp 0 refills it
+        K* hd = static_cast<K*>(sa.host_out) + cur.out;
+        const K* sk = rk + ok_ph;
+        if (phase_of(hd) == ok_ph) {
+          // same 16-byte phase as the staged block: 16-byte stores for the
+          // aligned interior, single elements at the two ends
+          const Window w = plan_window<sizeof(K)>(hd, static_cast<uint32_t>(cnt));
+          const uint32_t nsingle = w.head + w.tail;
+          for (uint32_t x = tid; x < nsingle; x += BLOCK) {
+            const uint32_t e = (x < w.head) ? x : static_cast<uint32_t>(cnt) - w.tail + (x - w.head);
+            hd[e] = sk[e];
+          }
+          uint4* hv = reinterpret_cast<uint4*>(hd + w.head);
+          const uint4* sv = reinterpret_cast<const uint4*>(sk + w.head);
+          for (uint32_t x = tid; x < w.body_bytes / 16; x += BLOCK) hv[x] = sv[x];
+        } else {
+          for (int x = tid; x < cnt; x += BLOCK) hd[x] = sk[x];
+        }
+        consumers_sync(BLOCK);
+      }
+    }
     if (wid == 0) {
-      if (cnt > 0) {
+      if (cnt > 0 && !to_host) {
         store_window(kd, rk + ok_ph, cnt, lane);
         if constexpr (HAS_V) store_window(vd, rv + ov_ph, cnt, lane);
       }
@@ -530,6 +563,22 @@ __global__ void __launch_bounds__(BLOCK + 32, (HAS_V || sizeof(K) == 8) ? 2 : 3)
       if (!failed && !w0_failed) note_ready(kc);
       st_release_cta_shared(&s_cons_done, 1u);  // the producer publishes the rest and leaves
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_copy_unmerged (host-buffer calls whose last merge passes write to host
+// memory): the packets that need no merge pass (at most one tile, sorted by
+// the tile sort into U) are copied from U to the caller's host array; one
+// CTA per packet, plain coalesced stores.
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ void k_copy_unmerged(const K* __restrict__ ku, K* hout, uint32_t npk, Tables tb) {
+  griddep_open();
+  for (uint32_t p = blockIdx.x; p < npk; p += gridDim.x) {
+    if (tb.unit_prefix[p + 1] - tb.unit_prefix[p] > 1) continue;  // merged: written by its last pass
+    const uint64_t b = tb.pkt_off[p], e = tb.pkt_off[p + 1];
+    for (uint64_t i = b + threadIdx.x; i < e; i += blockDim.x) hout[i] = ku[i];
   }
 }
 

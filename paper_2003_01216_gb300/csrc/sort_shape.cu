@@ -10,7 +10,7 @@
 
 namespace hs {
 hs_status HS_SHAPE_FN(void* keys, uint32_t* vals, size_t n, size_t nseg, const uint64_t* offs, const hs_opts& o,
-                      char* ws, uint32_t* err, cudaStream_t st, const void* src) {
-  return run_sort_ipt<HS_SHAPE_KEY, HS_SHAPE_IPT>(keys, vals, n, nseg, offs, o, ws, err, st, src);
+                      char* ws, uint32_t* err, cudaStream_t st, const void* src, int* host_done) {
+  return run_sort_ipt<HS_SHAPE_KEY, HS_SHAPE_IPT>(keys, vals, n, nseg, offs, o, ws, err, st, src, host_done);
 }
 }  // namespace hs

@@ -126,35 +126,48 @@ def test_caller_workspace(oracle):
 # also take the flipped-image pass, which then reads the device copy); with
 # partition 1 or n of at most one tile there is no histogram and the sort
 # copies the keys in first
-HOST_CASES = [("uniform1e9", 200_000, 10), ("int32full", 1_500_001, 10), ("uniform64", 777_777, 10),
-              ("uniform32", 300_003, 256), ("zipf", 250_000, 1), ("uniform31", 5_000, 10), ("uniform64", 1, 10)]
+# merge = 1 puts the merge passes in the persistent queue launch, whose last
+# pass of every packet writes straight back to pinned host memory (and a small
+# kernel copies the packets that need no merge pass: uniform [0, 2^31) at 100K
+# keys has a third packet of one tile); merge = 2 keeps a launch per pass and
+# a copy out after the sort
+HOST_CASES = [("uniform1e9", 200_000, 10, 2), ("int32full", 1_500_001, 10, 2), ("uniform64", 777_777, 10, 2),
+              ("uniform32", 300_003, 256, 2), ("zipf", 250_000, 1, 2), ("uniform31", 5_000, 10, 0),
+              ("uniform64", 1, 10, 0), ("uniform31", 100_000, 10, 1), ("int32full", 1_500_001, 10, 1),
+              ("uniform64", 777_777, 10, 1), ("zipf", 2_000_000, 10, 1), ("uniform32", 300_003, 256, 1),
+              ("uniform31", 250_000, 1, 1), ("equal", 400_000, 10, 1)]
 
 
-@pytest.mark.parametrize("dist,n,nb", HOST_CASES, ids=[f"{d}-{n}-{nb}" for d, n, nb in HOST_CASES])
-def test_host_buffers(oracle, dist, n, nb):
+@pytest.mark.parametrize("dist,n,nb,merge", HOST_CASES, ids=[f"{d}-{n}-{nb}-m{m}" for d, n, nb, m in HOST_CASES])
+def test_host_buffers(oracle, dist, n, nb, merge):
+    fan = 2 if merge == 1 else 0  # (the tuned rule takes fan-in 4 up to 2^21 keys)
     keys = I.generate(dist, n, seed=12)
     exp = oracle.sort(keys, nbuckets=nb)[0]
-    h = keys.copy()  # pageable: copied in by cudaMemcpyAsync
-    hs.sort_keys_host(h, partition=nb)
+    h = keys.copy()  # pageable: copied in and out by cudaMemcpyAsync
+    hs.sort_keys_host(h, partition=nb, merge=merge, fan_in=fan)
     assert_equal(h, exp, "host-buffer sort")
-    pinned = torch.from_numpy(keys.copy()).pin_memory()  # device-addressable: read by the sort itself
+    pinned = torch.from_numpy(keys.copy()).pin_memory()  # device-addressable: read (and written) by the sort itself
     for _ in range(2):  # the second call sorts sorted keys, same result
-        hs.sort_keys_host(pinned, partition=nb)
+        hs.sort_keys_host(pinned, partition=nb, merge=merge, fan_in=fan)
         assert hs.stream_error() == 0
         assert_equal(pinned.numpy(), exp, "pinned host-buffer sort")
-    # which path ran: the histogram that reads host memory, or a copy in
+    # which path ran: the histogram that reads host memory or a copy in; the
+    # merge queue writing back to host memory or a copy out
     pinned.copy_(torch.from_numpy(keys))
     hs.timing_read()
     hs.timing_enable(True)
     try:
-        hs.sort_keys_host(pinned, partition=nb)
+        hs.sort_keys_host(pinned, partition=nb, merge=merge, fan_in=fan)
         names = set(hs.timing_read())
     finally:
         hs.timing_enable(False)
     assert_equal(pinned.numpy(), exp, "pinned host-buffer sort, timed")
     code = {np.dtype(np.int32): 0, np.dtype(np.uint32): 1, np.dtype(np.uint64): 2}[keys.dtype]
-    fused = nb != 1 and n > hs.plan(code, n)["tile"]
+    plan = hs.plan(code, n, partition=nb, merge=merge, fan_in=fan)
+    fused = nb != 1 and n > plan["tile"]
     assert ("hist_copy_in" in names) == fused and ("copy_in" in names) == (not fused), sorted(names)
+    queue = merge == 1 and plan["fan_in"] == 2 and plan["merge_passes"] > 0
+    assert ("copy_unmerged" in names) == queue, sorted(names)
 
 
 def test_streams_do_not_share_work_space(oracle):

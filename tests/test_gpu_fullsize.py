@@ -58,6 +58,13 @@ def test_fullsize_plain_vs_oracle(oracle, dist):
     gk4, _, goff4 = gpu_sort(keys, fan_in=4)
     assert_equal(goff4, eoff, f"{dist} packet offsets (fan-in 4)")
     assert_equal(gk4, ek, f"{dist} sorted keys (fan-in 4)")
+    # through pinned host memory, as the end-to-end benchmark sorts: read by
+    # the histogram kernel, the last merge pass of every packet written back
+    # to host memory by the merge queue
+    pinned = torch.from_numpy(keys).pin_memory()
+    hs.sort_keys_host(pinned)
+    assert_equal(pinned.numpy(), ek, f"{dist} sorted keys through host memory")
+    del pinned
     if dist == "uniform31":
         # 256-bucket ablation: same unique sorted output, its own offsets
         gk2, _, goff2 = gpu_sort(keys, nb=256)
