@@ -210,6 +210,25 @@ def ncu_traffic(kernel: str, keys_per_launch: float):
     return rec["dram_bytes_per_key"] * keys_per_launch
 
 
+def merge_pass_roofline(launches: list, name: str, active: list, s: int, peak: float) -> dict:
+    """Achieved GB/s of every merge pass r = 1 .. P of one sort run with a
+    launch per pass: the pass's algorithmic bytes (it reads and writes the keys
+    of the packets that take part in it, 2 * s * active[r-1]) over the event
+    time of its merge launch.  Passes enqueued beyond the call's needs (the
+    worst case for its size) do no work and are left out."""
+    times = [ms for nm, ms in launches if nm == name]
+    passes = []
+    for r, keys in enumerate(active, start=1):
+        if r > len(times) or times[r - 1] <= 0:
+            break
+        gbs = 2 * s * keys / (times[r - 1] / 1e3) / 1e9
+        passes.append({"pass": r, "active_keys": keys, "ms": round(times[r - 1], 4), "achieved_gbs": round(gbs, 1),
+                       "frac": round(gbs / peak, 4), "frac_vs_nominal": round(gbs / NOMINAL_HBM_GBS, 4)})
+    corank_ms = sum(ms for nm, ms in launches if nm in ("corank", "bound4"))
+    return {"launch_style": "a co-rank (or sample-ranking) launch and a merge launch per pass, one instrumented sort",
+            "kernel": name, "passes": passes, "search_ms": round(corank_ms, 4)}
+
+
 def per_kernel_roofline(per_kernel: dict, steps: int, key_read: int, sn: int, merge_keys: int, s: int, mk: str,
                         peak: float) -> dict:
     """Achieved GB/s of each HBM pass of the sort: its algorithmic bytes per
@@ -371,15 +390,16 @@ def main():
         if has_vals:
             vals.copy_(vals_p)
 
-    def step(offsets=None):
+    def step(offsets=None, merge=None):
         # the packet offsets are an optional extra output (the byte model reads
         # them); the timed steps sort the way a caller without it would
+        m = mrg if merge is None else merge
         if has_vals:
             hs.sort_pairs(work, vals, partition=args.partition, packet_offsets=offsets, fan_in=args.fan_in,
-                          tile=args.tile, merge=mrg)
+                          tile=args.tile, merge=m)
         else:
             hs.sort_keys(work, partition=args.partition, packet_offsets=offsets, fan_in=args.fan_in, tile=args.tile,
-                         merge=mrg)
+                         merge=m)
 
     # warm-up (also sizes the work space outside the timed region; the last
     # one returns the packet offsets, identical for every step of one input)
@@ -423,6 +443,14 @@ def main():
         restore()
         step()
     per_kernel = hs.timing_read()
+    # per merge pass: one more instrumented sort with a launch per pass (the
+    # timed steps may run every pass in one persistent launch)
+    restore()
+    step(merge=2)  # warm: the per-pass kernels loaded and set up
+    restore()
+    hs.timing_read_launches()  # clear
+    step(merge=2)
+    pass_launches = hs.timing_read_launches()
     hs.timing_enable(False)
     if args.warmup == 0:  # no warm-up step returned the packet offsets
         restore()
@@ -453,6 +481,7 @@ def main():
     whole_gbs = b_alg / (mean_ms / 1e3) / 1e9
     floor_gbs = 2 * s * n / (mean_ms / 1e3) / 1e9
     per_pass = per_kernel_roofline(per_kernel, split_steps, key_bytes * n, s * n, sum(active), s, mk, peak)
+    merge_passes = merge_pass_roofline(pass_launches, "merge4" if plan["fan_in"] == 4 else "merge", active, s, peak)
 
     # end-to-end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -509,6 +538,7 @@ def main():
                            "floor_frac_vs_nominal": floor_gbs / NOMINAL_HBM_GBS,
                            "merge_passes": len(active), "tile": plan["tile"], "fan_in": plan["fan_in"]},
             "per_kernel_roofline": per_pass,
+            "merge_per_pass": merge_passes,
             "batch": extras.get("batch"),
             "serve": extras.get("serve"),
             "cpu_baseline": cpu,

@@ -231,6 +231,10 @@ typedef struct {
 hs_status hs_timing_enable(int on);
 /* Synchronises the device, returns up to `max` entries, clears the record. */
 hs_status hs_timing_read(hs_kernel_time* out, int max, int* count);
+/* The same record launch by launch, in launch order (launches = 1, total_ms =
+ * that launch's time): up to `max` entries, *count = how many were written;
+ * clears the record. */
+hs_status hs_timing_read_launches(hs_kernel_time* out, int max, int* count);
 
 /* Destroy every cached CUDA graph (see hs_opts.graph). */
 hs_status hs_graph_cache_clear(void);

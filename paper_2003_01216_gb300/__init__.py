@@ -14,7 +14,7 @@ from . import _native as N
 
 __all__ = [
     "sort_keys", "sort_pairs", "sort_batch", "sort_keys_host", "stream_error", "plan", "workspace_size",
-    "workspace_reserve", "workspace_release", "graph_cache_clear", "timing_enable", "timing_read", "kernel_launches", "HsError",
+    "workspace_reserve", "workspace_release", "graph_cache_clear", "timing_enable", "timing_read", "timing_read_launches", "kernel_launches", "HsError",
     "dtype_code",
 ]
 
@@ -171,6 +171,15 @@ def timing_read() -> dict[str, tuple[int, float]]:
     c = ctypes.c_int()
     N.check(N.lib().hs_timing_read(arr, 64, ctypes.byref(c)), "hs_timing_read")
     return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(c.value)}
+
+
+def timing_read_launches(max_launches: int = 4096) -> list[tuple[str, float]]:
+    """[(kernel name, ms)] launch by launch, in launch order, since the last
+    read (synchronises)."""
+    arr = (N.HsKernelTime * max_launches)()
+    c = ctypes.c_int()
+    N.check(N.lib().hs_timing_read_launches(arr, max_launches, ctypes.byref(c)), "hs_timing_read_launches")
+    return [(arr[i].name.decode(), arr[i].total_ms) for i in range(c.value)]
 
 
 def kernel_launches() -> int:

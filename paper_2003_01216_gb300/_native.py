@@ -19,7 +19,7 @@ HS_INT32, HS_UINT32, HS_UINT64 = 0, 1, 2
 EXPORTS = [
     "hs_sort_keys", "hs_sort_pairs", "hs_sort_batch", "hs_sort_keys_host", "hs_workspace_size",
     "hs_workspace_reserve", "hs_workspace_release", "hs_stream_error", "hs_plan_describe",
-    "hs_timing_enable", "hs_timing_read", "hs_kernel_launches", "hs_status_string", "hs_last_error",
+    "hs_timing_enable", "hs_timing_read", "hs_timing_read_launches", "hs_kernel_launches", "hs_status_string", "hs_last_error",
     "hs_sort_keys_noalloc", "hs_graph_cache_clear", "hs_tune_set", "hs_tune_get", "hs_tune_clear",
     "hs_tune_set_shape", "hs_tune_get_shape", "hs_tiles",
 ]
@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
         L.hs_plan_describe.argtypes = [i, sz, i, sz, p, p]
         L.hs_timing_enable.argtypes = [i]
         L.hs_timing_read.argtypes = [p, i, p]
+        L.hs_timing_read_launches.argtypes = [p, i, p]
         L.hs_kernel_launches.argtypes = []
         L.hs_kernel_launches.restype = ctypes.c_ulonglong
         L.hs_status_string.argtypes = [i]

@@ -577,6 +577,33 @@ hs_status hs_timing_enable(int on) {
   return HS_OK;
 }
 
+hs_status hs_timing_read_launches(hs_kernel_time* out, int max, int* count) {
+  if ((!out && max > 0) || max < 0) return HS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return HS_ERR_CUDA;
+  }
+  int c = 0;
+  for (auto& r : g_times) {
+    if (c < max) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      hs_kernel_time k{};
+      std::snprintf(k.name, sizeof(k.name), "%s", r.name);
+      k.launches = 1;
+      k.total_ms = ms;
+      out[c++] = k;
+    }
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_times.clear();
+  if (count) *count = c;
+  return HS_OK;
+}
+
 hs_status hs_timing_read(hs_kernel_time* out, int max, int* count) {
   std::lock_guard<std::mutex> lk(g_mu);
   cudaError_t e = cudaDeviceSynchronize();

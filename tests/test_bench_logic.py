@@ -93,3 +93,19 @@ def test_per_kernel_roofline_fractions():
     assert r["merge"]["launches_per_step"] == 14
     # a kernel that was not timed is left out
     assert "tilesort" not in bench.per_kernel_roofline({"merge": (1, 1.0)}, 1, 1, 1, 1, 4, "merge", 1.0)
+
+
+def test_merge_pass_roofline():
+    # three passes with active keys; launches in launch order, other kernels mixed in,
+    # and one extra enqueued pass that does no work
+    n = 1 << 20
+    active = [n, n, n // 2]
+    launches = [("hist", 0.1), ("corank", 0.01), ("merge", 0.5), ("corank", 0.01), ("merge", 0.25),
+                ("corank", 0.01), ("merge", 0.125), ("corank", 0.0), ("merge", 0.002)]
+    r = bench.merge_pass_roofline(launches, "merge", active, 4, 6800.0)
+    assert [p["pass"] for p in r["passes"]] == [1, 2, 3]
+    assert abs(r["passes"][0]["achieved_gbs"] - round(2 * 4 * n / 0.5e-3 / 1e9, 1)) < 1e-9
+    assert abs(r["passes"][2]["achieved_gbs"] - round(2 * 4 * (n // 2) / 0.125e-3 / 1e9, 1)) < 1e-9
+    assert abs(r["search_ms"] - 0.03) < 1e-9
+    # a missing launch ends the list
+    assert bench.merge_pass_roofline(launches[:3], "merge", active, 4, 6800.0)["passes"][-1]["pass"] == 1

@@ -35,6 +35,22 @@ def test_mix_equals_alone_and_oracle(oracle):
         assert np.array_equal(srv.results[r.rid], oracle.sort(keys)[0]), f"request {r.rid} vs oracle"
 
 
+def test_two_hundred_requests_vs_oracle(oracle):
+    # a seeded sample of over 200 requests of both key types, served with
+    # batching and single sorts overlapping on 8 streams: every result equals
+    # the oracle's sort of the same request's keys (made on the host by the
+    # seeded generator)
+    reqs = serve.make_requests(rate=50_000, duration=0.005, lo=1024, hi=1 << 17, seed=6)
+    assert len(reqs) >= 200
+    srv = serve.Server(slots=8, budget_bytes=1 << 30, small_keys=1 << 13, seed=6, keep_results=True)
+    stats = srv.run(reqs)
+    assert stats["batches"] > 0 and stats["singles"] > 0
+    assert {r.dtype_code for r in reqs} == {0, 2}
+    for r in reqs:
+        keys = I.generate(I.request_dist(r.dtype_code), r.n, seed=6, stream=r.rid)
+        assert np.array_equal(srv.results[r.rid], oracle.sort(keys)[0]), f"request {r.rid} vs oracle"
+
+
 def test_small_budget_still_serves_everything():
     reqs = serve.make_requests(rate=5_000, duration=0.01, lo=1024, hi=1 << 16, seed=4)
     srv = serve.Server(slots=4, budget_bytes=64 << 10, small_keys=1 << 12, seed=4, keep_results=True)
