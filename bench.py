@@ -17,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -251,6 +252,30 @@ def per_kernel_roofline(per_kernel: dict, steps: int, key_read: int, sn: int, me
 # --------------------------------------------------------------------------
 # reference arm and CPU baseline: the oracle on host cores
 # --------------------------------------------------------------------------
+def host_cpu() -> dict:
+    """The host the oracle runs on: logical CPUs and the CPU model as the
+    system reports it (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:  # noqa: BLE001
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
 def oracle_rate(dist: str, n_full: int, has_vals: bool, partition: int, sample: int, reps: int):
     import oracle
     from paper_2003_01216_gb300 import inputs as I
@@ -294,7 +319,8 @@ def run_reference(args, rank, world):
         "impl": "reference",
         "config": workload_config(args, dist, n, has_vals, world),
         "cpu_baseline": {"value": rate, "unit": "keys/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sample} keys of the workload's distribution per step (the full workload is {n})"},
+                         "sample": f"{sample} keys of the workload's distribution per step (the full workload is {n})",
+                         "host": host_cpu()},
         "e2e": {"value": rate, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -507,7 +533,8 @@ def main():
         sample = min(args.cpu_sample, n)
         rate, sec = oracle_rate(dist_name, n, has_vals, args.partition, sample, reps=1)
         cpu = {"value": rate, "unit": "keys/s", "cores": 1, "kind": "oracle",
-               "sample": f"one oracle sort of {sample} keys of the same distribution ({sec:.1f} s)"}
+               "sample": f"one oracle sort of {sample} keys of the same distribution ({sec:.1f} s)",
+               "host": host_cpu()}
 
     # configs 4 and 5 in brief, outside the timed region (one GPU only)
     extras = {}
