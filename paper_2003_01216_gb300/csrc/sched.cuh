@@ -29,6 +29,11 @@
 // while block k is merged (two stages, as k_merge), stores the merged block
 // by bulk copy and, once a store has completed, publishes it (release add on
 // the counter of the run it belongs to).
+//
+// A second instantiation (TO_HOST) serves sorts of keys in pinned host
+// memory: the blocks of every packet's last pass go from the stage straight
+// to the caller's host array (plain 16-byte stores by all merging warps),
+// and k_copy_unmerged moves the packets that needed no merge pass there.
 #pragma once
 #include "blockmerge.cuh"
 #include "merge.cuh"
