@@ -5,7 +5,12 @@ launch style, tile, values or not, device or host buffers) from a fixed seed;
 sizes are drawn near the edges the kernels care about (multiples of the
 packet-step block of 3840 keys and of the tile, plus or minus a few keys, and
 powers of two).  Each result is compared element by element with the
-oracle's sort (keys, and the stable order of the values)."""
+oracle's sort (keys, and the stable order of the values).
+
+HS_SWEEP_CASES / HS_SWEEP_FIRST (environment) widen the sweep: that many
+cases from that case index on (default 40 from 0)."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -20,7 +25,8 @@ DISTS = {0: ["uniform1e9", "uniform31", "zipf", "sorted", "reverse", "equal", "d
              "three_digit"],
          1: ["uniform32"],
          2: ["uniform64", "distinct2p24"]}
-N_CASES = 40
+N_CASES = int(os.environ.get("HS_SWEEP_CASES", "40"))
+FIRST = int(os.environ.get("HS_SWEEP_FIRST", "0"))
 
 
 def _case(i):
@@ -40,7 +46,7 @@ def _case(i):
     return code, dist, n, nb, fan, merge, tile, with_vals, host
 
 
-CASES = [_case(i) for i in range(N_CASES)]
+CASES = [_case(i) for i in range(FIRST, FIRST + N_CASES)]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[1]}-{c[2]}-nb{c[3]}-f{c[4]}m{c[5]}t{c[6]}{'-v' if c[7] else ''}"
