@@ -34,6 +34,16 @@
 // memory: the blocks of every packet's last pass go from the stage straight
 // to the caller's host array (plain 16-byte stores by all merging warps),
 // and k_copy_unmerged moves the packets that needed no merge pass there.
+// Those last passes are bound by the host link (~200 GB/s), the others by
+// HBM, so the instantiation orders the work to overlap the two (for packet
+// tables of at most kSchedSmemPackets entries): device tickets take every
+// packet's passes but its last, packet by packet (packet 0's passes first,
+// so its last pass can start early), and host tickets, from a second
+// counter, the last passes, packet by packet.  The first min(32, grid / 8)
+// CTAs take host tickets from the start; the others take device tickets and
+// then host tickets once the device tickets run out.  A host ticket depends
+// on device tickets only, a device ticket on smaller device tickets only, so
+// the progress argument above holds for each counter.
 #pragma once
 #include "blockmerge.cuh"
 #include "merge.cuh"
@@ -44,6 +54,17 @@ constexpr int kSchedRing = 16;   // records in flight between producer and consu
 constexpr int kSchedRound = 8;   // tickets claimed by the producer at once (four lanes each)
 constexpr uint32_t kSchedSmemPackets = 64;  // packet tables this small are read from shared memory
 constexpr uint32_t kSigNone = 0xffffffffu;
+constexpr uint32_t kSchedHostCtas = 32;  // TO_HOST: CTAs that take host tickets from the start (at most)
+
+// last p in [0, npk) with pre[p] <= t (pre non-decreasing)
+__device__ __forceinline__ uint32_t find_pre64(const uint64_t* pre, uint32_t npk, uint64_t t) {
+  uint32_t lo = 0, hi = npk;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (pre[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
   uint32_t v;
@@ -133,7 +154,7 @@ __device__ __forceinline__ void st_release_cta_shared(uint32_t* p, uint32_t v) {
 
 struct SchedArgs {
   uint32_t* done;       // (passes + 1) x units completion counters, zeroed
-  uint32_t* ticket;     // next ticket, zeroed
+  uint32_t* ticket;     // next ticket (64-bit), zeroed; TO_HOST: next host ticket at ticket + 2 (64-bit), zeroed
   int pass_limit;       // passes to run (testing: stop after pass r), else kMaxPasses
   int debug_drop;       // testing: the block of ticket 0 never publishes its completion
   uint64_t limit_ns;    // bound of every wait
@@ -204,6 +225,43 @@ __global__ void __launch_bounds__(BLOCK + 32, (HAS_V || sizeof(K) == 8) ? 2 : 3)
       tbp.unit_prefix = s_up;
       tbp.pkt_off = s_po;
     }
+    // TO_HOST, staged order: per packet the first device ticket (its passes
+    // 1 .. P-1, pass-major inside the packet) and the first host ticket (its
+    // pass P), in packet order
+    bool staged = false;
+    uint64_t dtotal = total, htotal = 0;
+    [[maybe_unused]] uint64_t* s_dpre = nullptr;
+    [[maybe_unused]] uint32_t* s_hpre = nullptr;
+    if constexpr (TO_HOST) {
+      __shared__ uint64_t s_dpre_[kSchedSmemPackets + 1];
+      __shared__ uint32_t s_hpre_[kSchedSmemPackets + 1];
+      s_dpre = s_dpre_;
+      s_hpre = s_hpre_;
+      staged = npk <= kSchedSmemPackets;
+      if (staged) {
+        if (lane == 0) {
+          uint64_t d = 0;
+          uint32_t h = 0;
+          for (uint32_t p = 0; p < npk; ++p) {
+            s_dpre[p] = d;
+            s_hpre[p] = h;
+            const uint32_t n = s_up[p + 1] - s_up[p];
+            const int P = min(ceil_log2(n), passes);
+            if (P >= 1) {
+              d += static_cast<uint64_t>(P - 1) * n;
+              h += n;
+            }
+          }
+          s_dpre[npk] = d;
+          s_hpre[npk] = h;
+        }
+        __syncwarp();
+        dtotal = s_dpre[npk];
+        htotal = s_hpre[npk];
+      }
+    }
+    const uint32_t nhost = min(kSchedHostCtas, gridDim.x / 8);
+    bool host_mode = staged && blockIdx.x < nhost;
     // Release the CTA's blocks whose stores are complete (any one lane at a
     // time; a lane that finds another one at it moves on).  Consecutive
     // blocks of the same run are added with one release: a release waits
@@ -227,19 +285,42 @@ __global__ void __launch_bounds__(BLOCK + 32, (HAS_V || sizeof(K) == 8) ? 2 : 3)
     bool stop = false;
     while (!stop) {
       uint64_t t0 = 0;
+      uint32_t hm = host_mode ? 1u : 0u;
       if (lane == 0) {
         pub();
-        t0 = atomicAdd(reinterpret_cast<unsigned long long*>(sa.ticket), kSchedRound);
+        if (!hm) {
+          t0 = atomicAdd(reinterpret_cast<unsigned long long*>(sa.ticket), kSchedRound);
+          if (staged && t0 >= dtotal) hm = 1;  // device tickets done: on to the host tickets
+        }
+        if (hm) t0 = atomicAdd(reinterpret_cast<unsigned long long*>(sa.ticket) + 1, kSchedRound);
       }
       t0 = __shfl_sync(0xffffffffu, t0, 0);
-      if (t0 >= total || *reinterpret_cast<volatile uint32_t*>(tb.err) != 0) break;
+      host_mode = __shfl_sync(0xffffffffu, hm, 0) != 0;
+      const uint64_t lim = staged ? (host_mode ? htotal : dtotal) : total;
+      if (t0 >= lim || *reinterpret_cast<volatile uint32_t*>(tb.err) != 0) break;
       // lanes 4i .. 4i+3 serve ticket t0 + i: two searches of two lanes
       const int i = lane >> 2, q = (lane >> 1) & 1, j = lane & 1;
       const uint64_t t = t0 + static_cast<uint64_t>(i);
-      const int r = static_cast<int>(t / units) + 1;
-      const uint32_t u = static_cast<uint32_t>(t % units);
+      int r = static_cast<int>(t / units) + 1;
+      uint32_t u = static_cast<uint32_t>(t % units);
+      if constexpr (TO_HOST) {
+        if (staged && t < lim) {
+          if (host_mode) {  // pass P of the packet
+            const uint32_t p = find_pkt(s_hpre, npk, static_cast<uint32_t>(t));
+            const uint32_t n = s_up[p + 1] - s_up[p];
+            r = min(ceil_log2(n), passes);
+            u = s_up[p] + static_cast<uint32_t>(t - s_hpre[p]);
+          } else {  // pass 1 + local / n of the packet, unit local % n
+            const uint32_t p = find_pre64(s_dpre, npk, t);
+            const uint32_t n = s_up[p + 1] - s_up[p];
+            const uint64_t local = t - s_dpre[p];
+            r = static_cast<int>(local / n) + 1;
+            u = s_up[p] + static_cast<uint32_t>(local % n);
+          }
+        }
+      }
       MergeGeom g;
-      const bool active = t < total && merge_geom<TILE>(tbp, npk, u, r, g);
+      const bool active = t < lim && merge_geom<TILE>(tbp, npk, u, r, g);
       // the runs of pass r-1 that this block reads, and the counter it publishes
       uint32_t sig = kSigNone;
       const uint32_t* dep0 = nullptr;
