@@ -135,7 +135,10 @@ HOST_CASES = [("uniform1e9", 200_000, 10, 2), ("int32full", 1_500_001, 10, 2), (
               ("uniform32", 300_003, 256, 2), ("zipf", 250_000, 1, 2), ("uniform31", 5_000, 10, 0),
               ("uniform64", 1, 10, 0), ("uniform31", 100_000, 10, 1), ("int32full", 1_500_001, 10, 1),
               ("uniform64", 777_777, 10, 1), ("zipf", 2_000_000, 10, 1), ("uniform32", 300_003, 256, 1),
-              ("uniform31", 250_000, 1, 1), ("equal", 400_000, 10, 1)]
+              ("uniform31", 250_000, 1, 1), ("equal", 400_000, 10, 1),
+              # ten packets of a few tiles each: many packets whose only merge pass is their last
+              # (host tickets only in the merge queue), then packets of two passes
+              ("uniform1e9", 158_720, 10, 1), ("uniform1e9", 317_445, 10, 1)]
 
 
 @pytest.mark.parametrize("dist,n,nb,merge", HOST_CASES, ids=[f"{d}-{n}-{nb}-m{m}" for d, n, nb, m in HOST_CASES])
