@@ -260,8 +260,7 @@ __global__ void __launch_bounds__(BLOCK + 32, (HAS_V || sizeof(K) == 8) ? 2 : 3)
         htotal = s_hpre[npk];
       }
     }
-    const uint32_t nhost = min(kSchedHostCtas, gridDim.x / 8);
-    bool host_mode = staged && blockIdx.x < nhost;
+    bool host_mode = staged && blockIdx.x < min(kSchedHostCtas, gridDim.x / 8);
     // Release the CTA's blocks whose stores are complete (any one lane at a
     // time; a lane that finds another one at it moves on).  Consecutive
     // blocks of the same run are added with one release: a release waits
@@ -285,17 +284,24 @@ __global__ void __launch_bounds__(BLOCK + 32, (HAS_V || sizeof(K) == 8) ? 2 : 3)
     bool stop = false;
     while (!stop) {
       uint64_t t0 = 0;
-      uint32_t hm = host_mode ? 1u : 0u;
-      if (lane == 0) {
-        pub();
-        if (!hm) {
-          t0 = atomicAdd(reinterpret_cast<unsigned long long*>(sa.ticket), kSchedRound);
-          if (staged && t0 >= dtotal) hm = 1;  // device tickets done: on to the host tickets
+      if constexpr (TO_HOST) {
+        uint32_t hm = host_mode ? 1u : 0u;
+        if (lane == 0) {
+          pub();
+          if (!hm) {
+            t0 = atomicAdd(reinterpret_cast<unsigned long long*>(sa.ticket), kSchedRound);
+            if (staged && t0 >= dtotal) hm = 1;  // device tickets done: on to the host tickets
+          }
+          if (hm) t0 = atomicAdd(reinterpret_cast<unsigned long long*>(sa.ticket) + 1, kSchedRound);
         }
-        if (hm) t0 = atomicAdd(reinterpret_cast<unsigned long long*>(sa.ticket) + 1, kSchedRound);
+        host_mode = __shfl_sync(0xffffffffu, hm, 0) != 0;
+      } else {
+        if (lane == 0) {
+          pub();
+          t0 = atomicAdd(reinterpret_cast<unsigned long long*>(sa.ticket), kSchedRound);
+        }
       }
       t0 = __shfl_sync(0xffffffffu, t0, 0);
-      host_mode = __shfl_sync(0xffffffffu, hm, 0) != 0;
       const uint64_t lim = staged ? (host_mode ? htotal : dtotal) : total;
       if (t0 >= lim || *reinterpret_cast<volatile uint32_t*>(tb.err) != 0) break;
       // lanes 4i .. 4i+3 serve ticket t0 + i: two searches of two lanes
