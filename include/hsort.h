@@ -164,8 +164,10 @@ hs_status hs_sort_batch(hs_dtype dtype, void* d_keys, uint32_t* d_vals, const ui
  * a histogram -- partition 1, or n of at most one tile -- copies them in
  * first); and when the call's merge passes run in one persistent launch
  * (hs_opts.merge), the last merge pass of every packet writes its blocks
- * straight into the host array and the packets that need no merge pass are
- * copied there by a small kernel, so no separate copy out follows.  Pageable
+ * straight into the host array (packet by packet, so that one packet's
+ * writes over the host link overlap the next packets' device passes) and
+ * the packets that need no merge pass are copied there by a small kernel,
+ * so no separate copy out follows.  Pageable
  * memory is copied in and out with cudaMemcpyAsync.  Same result either way.
  */
 hs_status hs_sort_keys_host(hs_dtype dtype, void* h_keys, size_t n, const hs_opts* opts, void* stream);
