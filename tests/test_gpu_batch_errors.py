@@ -268,6 +268,30 @@ def test_merge_queue_wait_expires_and_context_survives(oracle):
     assert_equal(gk, oracle.sort(keys)[0], "sort after an expired merge-queue wait")
 
 
+def test_host_merge_queue_wait_expires_and_context_survives(oracle):
+    # a host-buffer call whose merge passes run in the queue's host-memory
+    # instantiation (device tickets packet by packet, last passes from the
+    # second counter, a few CTAs on it from the start): the first device
+    # ticket's block never publishes its completion (debug flag 2, wait limit
+    # 2 ms), so the device tickets that read its run and the host tickets of
+    # its packet give up, and hs_stream_error reports HS_ERR_TIMEOUT
+    import ctypes
+
+    from paper_2003_01216_gb300 import _native as N
+    keys = I.generate("uniform31", 300_000, seed=17)
+    assert hs.plan(0, keys.size, fan_in=2, merge=1)["merge_passes"] >= 2
+    pinned = torch.from_numpy(keys.copy()).pin_memory()
+    o = N.make_opts(partition=10, fan_in=2, merge=1, debug_flags=2)
+    assert N.lib().hs_sort_keys_host(N.HS_INT32, pinned.data_ptr(), keys.size, ctypes.byref(o),
+                                      torch.cuda.current_stream().cuda_stream) == 0
+    assert hs.stream_error() == HS_TIMEOUT
+    # the context stays usable and the next call is correct
+    pinned.copy_(torch.from_numpy(keys))
+    hs.sort_keys_host(pinned, fan_in=2, merge=1)
+    assert hs.stream_error() == 0
+    assert_equal(pinned.numpy(), oracle.sort(keys)[0], "host-buffer sort after an expired merge-queue wait")
+
+
 @pytest.mark.parametrize("dist,n,with_vals", [("uniform31", 3_000_000, False), ("zipf", 1_500_000, True),
                                               ("uniform64", 1_000_000, True), ("sorted", 2_000_000, False)])
 def test_merge_queue_equals_per_pass_launches(oracle, dist, n, with_vals):
